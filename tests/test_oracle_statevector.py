@@ -58,3 +58,37 @@ def test_parity_columns_stay_in_sector():
     par = np.array([bin(x).count("1") & 1 for x in range(64)])
     assert np.abs(psi[0, par == 1]).max() < 1e-300 or np.abs(psi[0, par == 1]).max() == 0
     assert abs(np.linalg.norm(psi) - 1) < 1e-14
+
+
+def test_gate_application_and_hole_match_dense_embedding(rng):
+    # every ordered qubit pair, including pairs listed high-to-low
+    n = 4
+    G = rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))
+    psi = rng.standard_normal((3, 16)) + 1j * rng.standard_normal((3, 16))
+    phi = rng.standard_normal((3, 16)) + 1j * rng.standard_normal((3, 16))
+    for a in range(n):
+        for b in range(n):
+            if a == b:
+                continue
+            E = dense.embed(G, (a, b), n)
+            np.testing.assert_allclose(sv.apply_gate(G, (a, b), psi, n), psi @ E.T, atol=1e-14)
+            h = sv.hole(phi, psi, (a, b), n)
+            for x in range(4):
+                for y in range(4):
+                    e = np.zeros((4, 4)); e[x, y] = 1.0
+                    ref = np.sum(phi * (psi @ dense.embed(e, (a, b), n).T))
+                    assert abs(h[x, y] - ref) < 1e-13
+
+
+def test_periodic_wrap_bond_matches_dense():
+    # the periodic chain lists its wrap bond high-to-low: (L-1, 0)
+    L = 4
+    p = w.make_problem(L, 4, 0.3, seed=41, periodic=True)
+    assert any(a > b for a, b in p.pairs.tolist())
+    Um = model.target_unitary_dense(model.hamiltonian_dense(L, 1.0, 4.0, True), 0.3)
+    st = model.SectorTarget(L, 1.0, 4.0, 0.3, True)
+    Xraw = w.random_directions(p.n_params, 1, 5)
+    f, g, hv, Xt = sv.cost_grad_hvp(p, st, range(1 << p.n), Xraw, chunk=64)
+    assert abs(f - dense.cost(p, Um)) <= 1e-13 * 2 ** p.n
+    assert _rel(g, dense.rgrad(p, Um)) < 1e-12
+    assert _rel(hv[0], dense.rhess(p, Um, Xt[0], method="cauchy")) < 1e-11
