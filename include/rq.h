@@ -1,0 +1,199 @@
+/*
+ * rq.h -- C ABI of the GB300 matrix-free Riemannian circuit optimiser.
+ *
+ * Problem (paper Sec. "Problem statement and setup"): a sequence of two-qubit
+ * gates G_1..G_g (each a 4x4 unitary on a listed qubit pair, G_1 applied
+ * first) approximates a target U = exp(-iHt).  The cost is
+ *     f(G) = -Re Tr[U^dagger C(G)]                        (Eq. f_target)
+ * evaluated as a sum over computational basis columns j,
+ *     f(G) = -Re sum_j <j| U^dagger C(G) |j>             (Eq. f_target_sum_unit_vec)
+ * with no 2^n x 2^n matrix ever formed.  The library also returns the
+ * Riemannian gradient (Eq. def_grad, Eq. grad_proj) and Riemannian
+ * Hessian-vector products (Eq. vector_field_derivative, Eq. hessian_def,
+ * Appendix "Evaluating Hessian-vector products"), and runs one
+ * trust-region / truncated-CG iteration (Sec. "Riemannian optimization").
+ *
+ * Conventions shared by every call:
+ *  - qubit 0 is the most significant bit of an amplitude index;
+ *  - a gate on listed pair (a, b) is a 4x4 complex128 matrix, row-major,
+ *    interleaved (re, im) doubles, local index 2*bit_a + bit_b
+ *    (Eq. gate_application_neighboring and its general form);
+ *  - "gates" arrays hold one matrix per parameter gate: [n_params][4][4]
+ *    complex128 = 32 doubles per gate; the circuit maps sequential gate l to
+ *    parameter param_of[l] (tied copies, Sec. "Brick wall circuit layout");
+ *  - structure 1 = parity-conserving gates (Eq. paritygatematrix): entries
+ *    outside the pattern are ignored on input and zero on output;
+ *  - all results are sums over the current column range (rq_set_columns;
+ *    default: all 2^n basis columns).  Partial sums over disjoint ranges add
+ *    up to the full result (every output is linear in the per-column terms).
+ *
+ * Ownership: every pointer argument is owned by the caller; the library
+ * copies what it reads before returning (host variants) or in stream order
+ * (_dev variants) and keeps no caller pointer.  The library owns its device
+ * workspace (allocated at rq_setup_target, freed at rq_destroy).
+ *
+ * Errors: every call returns RQ_OK (0) or a negative rq_status; the text of
+ * the last error of a context is rq_last_error(ctx).  After an error the
+ * outputs are unspecified and the context stays usable, except after
+ * RQ_ECUDA from a sticky device error.  Calls on one context must not run
+ * concurrently from several host threads.
+ */
+#ifndef RQ_H
+#define RQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rq_ctx rq_ctx;
+typedef int rq_status;
+
+#define RQ_OK 0
+#define RQ_EINVAL (-1)   /* invalid argument (sizes, pairs, indices, NULL) */
+#define RQ_ENOMEM (-2)   /* device workspace does not fit */
+#define RQ_ECUDA (-3)    /* a CUDA runtime call failed */
+#define RQ_ETIMEOUT (-4) /* a bounded device wait expired */
+#define RQ_ESTATE (-5)   /* call out of order (no target set up yet) */
+
+/* Circuit topology (paper Sec. "Quantum circuits"): gate l acts on qubits
+ * pairs[2l], pairs[2l+1] (distinct, in [0, n_qubits)) with parameter gate
+ * param_of[l] in [0, n_params) (NULL: param_of[l] = l, n_params = n_gates).
+ * structure: 0 general U(4) gates, 1 parity-conserving gates. */
+typedef struct {
+    int n_qubits;
+    int n_gates;
+    int n_params;
+    int structure;
+    const int32_t *pairs;
+    const int32_t *param_of;
+} rq_circuit;
+
+/* Target U = exp(-i H t).  model 0: spinful Fermi-Hubbard chain (Eq. sfFH)
+ * on n_sites sites, qubit j = (site j, up), qubit n_sites + j = (site j,
+ * down), hopping -J on nearest-neighbour bonds of each spin chain (plus the
+ * wrap bond without Z string when periodic, Eq. slFH_qubit), on-site U.
+ * n_qubits of the circuit must equal 2 * n_sites. */
+typedef struct {
+    int model;
+    int n_sites;
+    int periodic;
+    double J;
+    double U;
+    double t;
+} rq_target;
+
+/* One trust-region iteration (Absil et al. Algorithm 10 with truncated CG,
+ * Algorithm 11; paper Sec. "Riemannian optimization").  In: radius,
+ * max_radius, rho_accept, kappa, theta, max_inner (0: tangent dimension).
+ * Out: f (cost at the input gates), f_new (cost at the candidate), rho,
+ * grad_norm, step_norm, accepted, n_inner, tcg_exit (0 residual small,
+ * 1 negative curvature, 2 hit the radius, 3 iteration cap); radius is
+ * updated in place. */
+typedef struct {
+    double radius;
+    double max_radius;
+    double rho_accept;
+    double kappa;
+    double theta;
+    int max_inner;
+    double f;
+    double f_new;
+    double rho;
+    double grad_norm;
+    double step_norm;
+    int accepted;
+    int n_inner;
+    int tcg_exit;
+} rq_tr_state;
+
+/* Sizes and counters of a set-up context (diagnostics and benchmarking). */
+typedef struct {
+    int n_qubits;
+    int n_gates;
+    int n_params;
+    int structure;
+    int64_t amplitudes_per_column;  /* 2^n, or 2^(n-1) for parity gates */
+    int64_t columns;                /* columns in the current range */
+    int columns_per_tile;           /* B: basis columns swept together */
+    int n_tiles;
+    int max_dirs;                   /* HVP directions swept together */
+    int64_t workspace_bytes;        /* device memory held by the context */
+    int64_t target_entries;         /* complex entries of the stored U blocks */
+    int64_t kernel_launches;        /* kernels launched since rq_create */
+} rq_info_t;
+
+/* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to
+ * run on, or NULL to create a private stream.  *out receives the context. */
+rq_status rq_create(rq_ctx **out, int device, void *cuda_stream);
+
+/* Free the context and all its device memory.  NULL is accepted. */
+rq_status rq_destroy(rq_ctx *ctx);
+
+/* Build the device-resident target and workspace for a circuit.  The matrix
+ * -free action of U (paper Sec. "Objective function and matrix-free
+ * evaluation") is realised by per-sector blocks: H conserves the spin-resolved
+ * particle numbers, so U is block diagonal over (N_up, N_down) sectors; each
+ * block is built on the device by a Chebyshev expansion of exp(-iHt) with the
+ * sparse H.  Resets the column range to all 2^n columns.  Errors: RQ_EINVAL
+ * for an invalid circuit/target, RQ_ENOMEM if the workspace does not fit. */
+rq_status rq_setup_target(rq_ctx *ctx, const rq_target *target, const rq_circuit *circuit);
+
+/* Restrict the basis sum to columns j in [col_begin, col_end) (shards of
+ * Sec. "Parallelization").  RQ_EINVAL unless 0 <= begin <= end <= 2^n. */
+rq_status rq_set_columns(rq_ctx *ctx, int64_t col_begin, int64_t col_end);
+
+/* Tuning: columns per tile (a power of two, 0 = automatic) and the number of
+ * HVP directions swept together (1..4, 0 = automatic).  Reallocates the
+ * workspace; RQ_ENOMEM if it does not fit. */
+rq_status rq_set_tile(rq_ctx *ctx, int columns_per_tile, int max_dirs);
+
+/* f(G) over the column range (Eq. f_target_sum_unit_vec).  gates: host
+ * [n_params][4][4] complex128; f: host double. */
+rq_status rq_cost(rq_ctx *ctx, const double *gates, double *f);
+
+/* f and the Riemannian gradient grad f = P_G(d_x f + i d_y f) (Eq. def_grad,
+ * Eq. grad_proj; forward and backward pass of Sec. "Efficient gradient and
+ * Hessian computation"), tied copies summed.  rgrad: host [n_params][4][4]
+ * complex128 (may be NULL). */
+rq_status rq_grad(rq_ctx *ctx, const double *gates, double *f, double *rgrad);
+
+/* f, the Riemannian gradient and k Riemannian Hessian-vector products
+ * Hess f(G)[X_i] (Eq. hessian_def; forward mode then reverse, Appendix
+ * "Evaluating Hessian-vector products").  dirs: host [k][n_params][4][4]
+ * complex128 raw directions; each is first projected onto the tangent space
+ * (P_G, Eq. proj_tangent, then the parity pattern).  hvps: host
+ * [k][n_params][4][4].  k >= 0; rgrad/hvps may be NULL. */
+rq_status rq_hvp(rq_ctx *ctx, const double *gates, const double *dirs, int k,
+                 double *f, double *rgrad, double *hvps);
+
+/* Device-pointer variants of the three calls above: every pointer is device
+ * memory of the same shape, work is queued on the context stream and the
+ * call returns without synchronising. */
+rq_status rq_cost_dev(rq_ctx *ctx, const double *gates, double *f);
+rq_status rq_grad_dev(rq_ctx *ctx, const double *gates, double *f, double *rgrad);
+rq_status rq_hvp_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k,
+                     double *f, double *rgrad, double *hvps);
+
+/* One trust-region iteration on the host gates (in/out: replaced by the
+ * candidate when accepted).  Every cost, gradient and HVP inside runs on the
+ * device over the current column range. */
+rq_status rq_tr_step(rq_ctx *ctx, double *gates, rq_tr_state *state);
+
+/* Column U|j> of the stored target as 2^n complex128 (host `out`, zero
+ * outside the sector of j).  RQ_EINVAL unless 0 <= j < 2^n. */
+rq_status rq_target_column(rq_ctx *ctx, int64_t j, double *out);
+
+/* Sizes and counters of the context. */
+rq_status rq_get_info(const rq_ctx *ctx, rq_info_t *info);
+
+/* Text of the last error on this context ("" if none); valid until the next
+ * call on the context.  NULL ctx: the last rq_create failure. */
+const char *rq_last_error(const rq_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RQ_H */

@@ -1,0 +1,777 @@
+// C ABI entry points: context, target set-up, column tiles, workspace and the
+// tile-by-tile sweep schedule of one evaluation.
+//
+// One evaluation sums over basis columns (Eq. f_target_sum_unit_vec) tile by
+// tile.  For a tile of B columns:
+//   1. psi_0 = |j_b> for every column b;
+//   2. forward pass, caching every psi_l (Fig. forward_pass) and, for each
+//      HVP direction swept together, the tangent psi'_l;
+//   3. lambda_g = U|j_b> and the cost summands (target blocks, Eq.
+//      f_target_sum_unit_vec);
+//   4. backward pass, gate by gate in reverse: direction steps first (they
+//      read lambda_l), then the base step (environment E_l, lambda update),
+//      per-CTA environment partials (Fig. backward_pass_gate_gradient);
+//   5. per-gate partials summed in CTA order into the evaluation's
+//      accumulators.
+// After the last tile one kernel turns the accumulators into f, the
+// Riemannian gradient and the HVPs.  Work for one context is queued on its
+// stream in a fixed order, so results are reproducible bit for bit.
+#include "rq_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+using rq::GateGeom;
+
+struct rq_ctx {
+    int device = 0;
+    int sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    // problem
+    bool ready = false;
+    rq_target tgt{};
+    int n = 0, L = 0, g = 0, P = 0, structure = 0;
+    std::vector<int32_t> pairs, param_of;
+    std::vector<GateGeom> geo;
+    long long n_store = 0;
+    // sectors of the target
+    int S = 0;
+    std::vector<long long> off_basis, off_u;
+    std::vector<int32_t> basis_h, sec_of_h, pos_h;
+    int32_t *d_sec_of = nullptr, *d_pos = nullptr, *d_basis = nullptr;
+    long long *d_off_basis = nullptr, *d_off_u = nullptr;
+    double2 *d_U = nullptr;
+    long long u_entries = 0;
+    // columns and tiles
+    long long c0 = 0, c1 = 0;
+    int B = 0, log2B = 0, n_tiles = 0, kc = 1;
+    int user_B = 0, user_kc = 0;
+    std::vector<int> tile_parity;
+    int32_t *d_cols = nullptr;
+    // workspace
+    double2 *d_psi = nullptr, *d_dpsi = nullptr, *d_lam = nullptr, *d_dlam = nullptr;
+    double *d_part = nullptr, *d_partd = nullptr;
+    int ncta = 0;
+    double *d_env = nullptr, *d_envd = nullptr;
+    int envd_cap = 0;
+    double *d_fpart = nullptr, *d_facc = nullptr;
+    double2 *d_gates = nullptr, *d_in_gates = nullptr;
+    double2 *d_dirs = nullptr, *d_dirs_raw = nullptr;
+    int dirs_cap = 0;
+    int32_t *d_param_of = nullptr;
+    double *d_out = nullptr;
+    long long out_cap = 0;
+    long long problem_bytes = 0, work_bytes = 0, small_bytes = 0;
+    long long launches = 0;
+};
+
+namespace {
+
+std::string g_create_error;
+
+rq_status fail(rq_ctx *ctx, rq_status code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf; else g_create_error = buf;
+    return code;
+}
+
+#define RQ_CUDA(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) return fail(ctx, RQ_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define RQ_LAUNCHED()                                                                     \
+    do {                                                                                  \
+        ++ctx->launches;                                                                  \
+        cudaError_t e_ = cudaGetLastError();                                              \
+        if (e_ != cudaSuccess) return fail(ctx, RQ_ECUDA, "kernel launch: %s", cudaGetErrorString(e_)); \
+    } while (0)
+
+#define RQ_TRY(expr)                 \
+    do {                             \
+        rq_status s_ = (expr);       \
+        if (s_ != RQ_OK) return s_;  \
+    } while (0)
+
+template <typename T>
+rq_status dev_alloc(rq_ctx *ctx, T **p, long long count, long long &counter) {
+    *p = nullptr;
+    if (count <= 0) return RQ_OK;
+    const size_t bytes = (size_t)count * sizeof(T);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(ctx, RQ_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    counter += (long long)bytes;
+    return RQ_OK;
+}
+
+template <typename T>
+void dev_free(T *&p) {
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+void free_workspace(rq_ctx *ctx) {
+    dev_free(ctx->d_psi);
+    dev_free(ctx->d_dpsi);
+    dev_free(ctx->d_lam);
+    dev_free(ctx->d_dlam);
+    dev_free(ctx->d_part);
+    dev_free(ctx->d_partd);
+    dev_free(ctx->d_fpart);
+    dev_free(ctx->d_cols);
+    ctx->work_bytes = 0;
+}
+
+void free_small(rq_ctx *ctx) {
+    dev_free(ctx->d_env);
+    dev_free(ctx->d_envd);
+    dev_free(ctx->d_facc);
+    dev_free(ctx->d_gates);
+    dev_free(ctx->d_in_gates);
+    dev_free(ctx->d_dirs);
+    dev_free(ctx->d_dirs_raw);
+    dev_free(ctx->d_param_of);
+    dev_free(ctx->d_out);
+    ctx->envd_cap = ctx->dirs_cap = 0;
+    ctx->out_cap = 0;
+    ctx->small_bytes = 0;
+}
+
+void free_problem(rq_ctx *ctx) {
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    free_workspace(ctx);
+    free_small(ctx);
+    dev_free(ctx->d_sec_of);
+    dev_free(ctx->d_pos);
+    dev_free(ctx->d_basis);
+    dev_free(ctx->d_off_basis);
+    dev_free(ctx->d_off_u);
+    dev_free(ctx->d_U);
+    ctx->problem_bytes = 0;
+    ctx->ready = false;
+}
+
+int ilog2(long long v) {
+    int r = 0;
+    while ((1LL << r) < v) ++r;
+    return r;
+}
+
+// Column lists of the current range: one list (general gates) or the even-
+// then the odd-parity columns (parity gates: every tile shares one parity).
+void column_groups(const rq_ctx *ctx, std::vector<std::vector<int32_t>> &groups, std::vector<int> &parity) {
+    groups.clear();
+    parity.clear();
+    if (ctx->structure == 1) {
+        std::vector<int32_t> ev, od;
+        for (long long j = ctx->c0; j < ctx->c1; ++j) (__builtin_popcountll(j) & 1 ? od : ev).push_back((int32_t)j);
+        groups.push_back(std::move(ev));
+        parity.push_back(0);
+        groups.push_back(std::move(od));
+        parity.push_back(1);
+    } else {
+        std::vector<int32_t> all;
+        for (long long j = ctx->c0; j < ctx->c1; ++j) all.push_back((int32_t)j);
+        groups.push_back(std::move(all));
+        parity.push_back(0);
+    }
+}
+
+long long bytes_per_column(const rq_ctx *ctx, int kc) {
+    const long long sets = (long long)(1 + kc) * (ctx->g + 1) + 1 + kc;
+    return sets * ctx->n_store * (long long)sizeof(double2);
+}
+
+// Choose B (columns per tile) and kc (directions per sweep), build the tile
+// column table and allocate the sweep workspace.
+rq_status rebuild_tiles(rq_ctx *ctx) {
+    RQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    free_workspace(ctx);
+    std::vector<std::vector<int32_t>> groups;
+    std::vector<int> gpar;
+    column_groups(ctx, groups, gpar);
+    long long largest = 1;
+    for (auto &gr : groups) largest = std::max<long long>(largest, (long long)gr.size());
+    const int bcap = ctx->user_B > 0 ? ctx->user_B : (int)std::min<long long>(512, 1LL << ilog2(largest));
+    size_t free_b = 0, total_b = 0;
+    RQ_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const double budget = std::min(0.6 * (double)free_b, 96.0 * (1LL << 30));
+    int B = 0, kc = 1;
+    const int kc_opts[2] = {rq::kMaxDirs, 1};
+    const int n_opts = ctx->user_kc > 0 ? 1 : 2;
+    for (int o = 0; o < n_opts; ++o) {
+        const int k = ctx->user_kc > 0 ? ctx->user_kc : kc_opts[o];
+        int b = bcap;
+        while (b > 1 && (double)b * bytes_per_column(ctx, k) > budget) b >>= 1;
+        if ((double)b * bytes_per_column(ctx, k) > budget) continue;
+        if (o + 1 < n_opts && b < std::min(bcap, 256)) continue;
+        B = b;
+        kc = k;
+        break;
+    }
+    if (B == 0)
+        return fail(ctx, RQ_ENOMEM, "one column needs %lld bytes of workspace, %.0f available",
+                    bytes_per_column(ctx, 1), budget);
+    ctx->B = B;
+    ctx->log2B = ilog2(B);
+    ctx->kc = kc;
+    std::vector<int32_t> cols;
+    ctx->tile_parity.clear();
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        const auto &gr = groups[gi];
+        for (size_t s = 0; s < gr.size(); s += B) {
+            for (int b = 0; b < B; ++b) cols.push_back(s + b < gr.size() ? gr[s + b] : -1);
+            ctx->tile_parity.push_back(gpar[gi]);
+        }
+    }
+    ctx->n_tiles = (int)ctx->tile_parity.size();
+    const long long tile = ctx->n_store * B;
+    const long long items = std::max<long long>(1, ctx->n_store / 4 * B);
+    ctx->ncta = (int)std::min<long long>((long long)ctx->sms * rq::kCtasPerSm, (items + rq::kThreads - 1) / rq::kThreads);
+    RQ_TRY(dev_alloc(ctx, &ctx->d_psi, tile * (ctx->g + 1), ctx->work_bytes));
+    RQ_TRY(dev_alloc(ctx, &ctx->d_dpsi, tile * (ctx->g + 1) * kc, ctx->work_bytes));
+    RQ_TRY(dev_alloc(ctx, &ctx->d_lam, tile, ctx->work_bytes));
+    RQ_TRY(dev_alloc(ctx, &ctx->d_dlam, tile * kc, ctx->work_bytes));
+    RQ_TRY(dev_alloc(ctx, &ctx->d_part, (long long)ctx->g * ctx->ncta * rq::kEnvDoubles, ctx->work_bytes));
+    RQ_TRY(dev_alloc(ctx, &ctx->d_partd, (long long)kc * ctx->g * ctx->ncta * rq::kEnvDoubles, ctx->work_bytes));
+    RQ_TRY(dev_alloc(ctx, &ctx->d_fpart, B, ctx->work_bytes));
+    if (!cols.empty()) {
+        RQ_TRY(dev_alloc(ctx, &ctx->d_cols, (long long)cols.size(), ctx->work_bytes));
+        RQ_CUDA(cudaMemcpyAsync(ctx->d_cols, cols.data(), cols.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+        RQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    return RQ_OK;
+}
+
+rq_status ensure_small(rq_ctx *ctx, int k) {
+    if (k > ctx->dirs_cap) {
+        RQ_CUDA(cudaStreamSynchronize(ctx->stream));
+        dev_free(ctx->d_dirs);
+        dev_free(ctx->d_dirs_raw);
+        dev_free(ctx->d_envd);
+        dev_free(ctx->d_out);
+        ctx->out_cap = 0;
+        const int cap = std::max(k, 4);
+        RQ_TRY(dev_alloc(ctx, &ctx->d_dirs, (long long)cap * ctx->P * 16, ctx->small_bytes));
+        RQ_TRY(dev_alloc(ctx, &ctx->d_dirs_raw, (long long)cap * ctx->P * 16, ctx->small_bytes));
+        RQ_TRY(dev_alloc(ctx, &ctx->d_envd, (long long)cap * ctx->g * rq::kEnvDoubles, ctx->small_bytes));
+        ctx->dirs_cap = ctx->envd_cap = cap;
+    }
+    const long long need = 1 + (long long)(1 + ctx->dirs_cap) * ctx->P * 32;
+    if (need > ctx->out_cap) {
+        dev_free(ctx->d_out);
+        RQ_TRY(dev_alloc(ctx, &ctx->d_out, need, ctx->small_bytes));
+        ctx->out_cap = need;
+    }
+    return RQ_OK;
+}
+
+rq::TargetDev target_dev(const rq_ctx *ctx) {
+    rq::TargetDev t;
+    t.sec_of = ctx->d_sec_of;
+    t.pos = ctx->d_pos;
+    t.basis = ctx->d_basis;
+    t.off_basis = ctx->d_off_basis;
+    t.off_u = ctx->d_off_u;
+    t.U = ctx->d_U;
+    return t;
+}
+
+// Build the per-sector target blocks on the device (Chebyshev expansion).
+rq_status build_target(rq_ctx *ctx) {
+    const int n = ctx->n, L = ctx->L;
+    const long long dim = 1LL << n, lowmask = (1LL << L) - 1;
+    ctx->S = (L + 1) * (L + 1);
+    std::vector<long long> count(ctx->S, 0);
+    ctx->sec_of_h.assign(dim, 0);
+    ctx->pos_h.assign(dim, 0);
+    for (long long x = 0; x < dim; ++x) {
+        const int s = __builtin_popcountll(x >> L) * (L + 1) + __builtin_popcountll(x & lowmask);
+        ctx->sec_of_h[x] = s;
+        ctx->pos_h[x] = (int32_t)count[s]++;
+    }
+    ctx->off_basis.assign(ctx->S + 1, 0);
+    ctx->off_u.assign(ctx->S + 1, 0);
+    for (int s = 0; s < ctx->S; ++s) {
+        ctx->off_basis[s + 1] = ctx->off_basis[s] + count[s];
+        ctx->off_u[s + 1] = ctx->off_u[s] + count[s] * count[s];
+    }
+    ctx->basis_h.assign(dim, 0);
+    for (long long x = 0; x < dim; ++x) ctx->basis_h[ctx->off_basis[ctx->sec_of_h[x]] + ctx->pos_h[x]] = (int32_t)x;
+    ctx->u_entries = ctx->off_u[ctx->S];
+    std::vector<long long> sizes(count.begin(), count.end());
+
+    // hopping bonds of both spin chains as bit masks (qubit q <-> bit n-1-q)
+    std::vector<long long> bonds;
+    for (int off = 0; off <= L; off += L) {
+        for (int j = 0; j + 1 < L; ++j)
+            bonds.push_back((1LL << (n - 1 - off - j)) | (1LL << (n - 2 - off - j)));
+        if (ctx->tgt.periodic && L > 2) bonds.push_back((1LL << (n - 1 - off - (L - 1))) | (1LL << (n - 1 - off)));
+    }
+    // Gershgorin interval of H
+    const double J = ctx->tgt.J, U = ctx->tgt.U, t = ctx->tgt.t;
+    double emin = 1e300, emax = -1e300;
+    for (long long x = 0; x < dim; ++x) {
+        const double diag = U * (double)__builtin_popcountll((x >> L) & (x & lowmask));
+        int flips = 0;
+        for (long long mk : bonds) {
+            const long long bits = x & mk;
+            flips += (bits != 0 && bits != mk);
+        }
+        emin = std::min(emin, diag - std::fabs(J) * flips);
+        emax = std::max(emax, diag + std::fabs(J) * flips);
+    }
+    const double alpha = 0.5 * (emax - emin), beta = 0.5 * (emax + emin);
+    const double xarg = alpha * std::fabs(t);
+    std::vector<double> jv;
+    int K = 0;
+    if (alpha > 0.0 && xarg > 0.0) {
+        const int kmax = (int)(1.5 * xarg) + 60;
+        rq::bessel_j_table(xarg, kmax, jv);
+        for (int k = 0; k <= kmax; ++k)
+            if (std::fabs(jv[k]) > 1e-19) K = k;
+    } else {
+        jv.assign(1, 1.0);
+    }
+    const double ph = -beta * t;  // exp(-i beta t)
+    auto coef = [&](int k) {
+        // (2 - delta_k0) (-i)^k J_k(alpha t) exp(-i beta t); J_k(-x) = (-1)^k J_k(x)
+        double a = (k == 0 ? 1.0 : 2.0) * jv[k] * ((t < 0 && (k & 1)) ? -1.0 : 1.0);
+        double re = 0, im = 0;  // a * (-i)^k
+        switch (k & 3) {
+            case 0: re = a; break;
+            case 1: im = -a; break;
+            case 2: re = -a; break;
+            default: im = a; break;
+        }
+        return make_double2(re * std::cos(ph) - im * std::sin(ph), re * std::sin(ph) + im * std::cos(ph));
+    };
+
+    RQ_TRY(dev_alloc(ctx, &ctx->d_sec_of, dim, ctx->problem_bytes));
+    RQ_TRY(dev_alloc(ctx, &ctx->d_pos, dim, ctx->problem_bytes));
+    RQ_TRY(dev_alloc(ctx, &ctx->d_basis, dim, ctx->problem_bytes));
+    RQ_TRY(dev_alloc(ctx, &ctx->d_off_basis, ctx->S + 1, ctx->problem_bytes));
+    RQ_TRY(dev_alloc(ctx, &ctx->d_off_u, ctx->S + 1, ctx->problem_bytes));
+    RQ_TRY(dev_alloc(ctx, &ctx->d_U, ctx->u_entries, ctx->problem_bytes));
+    RQ_CUDA(cudaMemcpyAsync(ctx->d_sec_of, ctx->sec_of_h.data(), dim * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    RQ_CUDA(cudaMemcpyAsync(ctx->d_pos, ctx->pos_h.data(), dim * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    RQ_CUDA(cudaMemcpyAsync(ctx->d_basis, ctx->basis_h.data(), dim * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    RQ_CUDA(cudaMemcpyAsync(ctx->d_off_basis, ctx->off_basis.data(), (ctx->S + 1) * sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
+    RQ_CUDA(cudaMemcpyAsync(ctx->d_off_u, ctx->off_u.data(), (ctx->S + 1) * sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
+
+    long long scratch = 0;
+    double *tA = nullptr, *tB = nullptr;
+    long long *d_sizes = nullptr, *d_bonds = nullptr;
+    rq_status st = dev_alloc(ctx, &tA, ctx->u_entries, scratch);
+    if (st == RQ_OK) st = dev_alloc(ctx, &tB, ctx->u_entries, scratch);
+    if (st == RQ_OK) st = dev_alloc(ctx, &d_sizes, ctx->S, scratch);
+    if (st == RQ_OK) st = dev_alloc(ctx, &d_bonds, (long long)std::max<size_t>(1, bonds.size()), scratch);
+    if (st == RQ_OK) {
+        cudaMemcpyAsync(d_sizes, sizes.data(), ctx->S * sizeof(long long), cudaMemcpyHostToDevice, ctx->stream);
+        if (!bonds.empty())
+            cudaMemcpyAsync(d_bonds, bonds.data(), bonds.size() * sizeof(long long), cudaMemcpyHostToDevice, ctx->stream);
+        const rq::TargetDev td = target_dev(ctx);
+        rq::launch_cheb_init(ctx->d_off_u, d_sizes, ctx->S, ctx->u_entries, tA, ctx->d_U, coef(0), ctx->stream);
+        ++ctx->launches;
+        const double dscale = alpha > 0 ? 1.0 / alpha : 0.0, hop = alpha > 0 ? -J / alpha : 0.0;
+        double *prev = tA, *cur = tB;
+        for (int k = 1; k <= K; ++k) {
+            if (k == 1) {
+                rq::launch_cheb_step(td, ctx->S, ctx->u_entries, prev, cur, ctx->d_U, coef(1), 1.0, 1,
+                                     dscale, beta, hop, d_bonds, (int)bonds.size(), L, U, ctx->stream);
+            } else {
+                rq::launch_cheb_step(td, ctx->S, ctx->u_entries, cur, prev, ctx->d_U, coef(k), 2.0, 0,
+                                     dscale, beta, hop, d_bonds, (int)bonds.size(), L, U, ctx->stream);
+                std::swap(prev, cur);
+            }
+            ++ctx->launches;
+        }
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) st = fail(ctx, RQ_ECUDA, "target build: %s", cudaGetErrorString(e));
+    }
+    dev_free(tA);
+    dev_free(tB);
+    dev_free(d_sizes);
+    dev_free(d_bonds);
+    return st;
+}
+
+// One evaluation over the column range; every pointer is device memory.
+rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, bool want_env,
+                   double *f_out, double *rgrad, double *hvps) {
+    if (!ctx->ready) return fail(ctx, RQ_ESTATE, "no target set up (call rq_setup_target first)");
+    if (k < 0) return fail(ctx, RQ_EINVAL, "k = %d < 0", k);
+    if (!gates) return fail(ctx, RQ_EINVAL, "gates is NULL");
+    if (k > 0 && !dirs) return fail(ctx, RQ_EINVAL, "dirs is NULL with k = %d", k);
+    RQ_TRY(ensure_small(ctx, k));
+    cudaStream_t s = ctx->stream;
+    const int g = ctx->g, P = ctx->P;
+    rq::launch_mask_gates(reinterpret_cast<const double2 *>(gates), ctx->d_gates, P, ctx->structure, s);
+    RQ_LAUNCHED();
+    if (k > 0) {
+        rq::launch_project_dirs(ctx->d_gates, reinterpret_cast<const double2 *>(dirs), ctx->d_dirs, P, k,
+                                ctx->structure, s);
+        RQ_LAUNCHED();
+    }
+    RQ_CUDA(cudaMemsetAsync(ctx->d_env, 0, sizeof(double) * g * rq::kEnvDoubles, s));
+    if (k > 0) RQ_CUDA(cudaMemsetAsync(ctx->d_envd, 0, sizeof(double) * (size_t)k * g * rq::kEnvDoubles, s));
+    RQ_CUDA(cudaMemsetAsync(ctx->d_facc, 0, sizeof(double), s));
+
+    const int B = ctx->B;
+    const long long tile = ctx->n_store * B;
+    const long long set = tile * (g + 1);  // one checkpoint set
+    const bool backward = want_env || k > 0;
+    const int n_chunks = k == 0 ? 1 : (k + ctx->kc - 1) / ctx->kc;
+    for (int ch = 0; ch < n_chunks; ++ch) {
+        const int d0 = ch * ctx->kc;
+        const int kd = k == 0 ? 0 : std::min(ctx->kc, k - d0);
+        const bool first = ch == 0;
+        for (int ti = 0; ti < ctx->n_tiles; ++ti) {
+            const int32_t *cols = ctx->d_cols + (long long)ti * B;
+            const int par = ctx->tile_parity[ti];
+            RQ_CUDA(cudaMemsetAsync(ctx->d_psi, 0, sizeof(double2) * tile, s));
+            rq::launch_init_unit(ctx->d_psi, cols, B, ctx->log2B, ctx->n_store, ctx->structure, s);
+            RQ_LAUNCHED();
+            for (int d = 0; d < kd; ++d) RQ_CUDA(cudaMemsetAsync(ctx->d_dpsi + d * set, 0, sizeof(double2) * tile, s));
+            // forward pass
+            for (int l = 0; l < g; ++l) {
+                const GateGeom &geo = ctx->geo[l];
+                rq::FwdArgs a;
+                a.psi_in = ctx->d_psi + l * tile;
+                a.psi_out = ctx->d_psi + (l + 1) * tile;
+                a.dpsi_in = ctx->d_dpsi + l * tile;
+                a.dpsi_out = ctx->d_dpsi + (l + 1) * tile;
+                a.dir_stride = set;
+                a.kdirs = kd;
+                a.gate = ctx->d_gates + (long long)geo.param * 16;
+                a.dirs = ctx->d_dirs + ((long long)d0 * P + geo.param) * 16;
+                a.xdir_stride = (long long)P * 16;
+                a.geo = geo;
+                a.log2B = ctx->log2B;
+                a.tile_parity = par;
+                a.n_items = (geo.mode == rq::kParity2 ? ctx->n_store / 2 : ctx->n_store / 4) * B;
+                rq::launch_fwd(a, ctx->ncta, s);
+                RQ_LAUNCHED();
+            }
+            // adjoint start lambda_g = U|j> and the cost summands
+            RQ_CUDA(cudaMemsetAsync(ctx->d_lam, 0, sizeof(double2) * tile, s));
+            rq::launch_scatter_target(target_dev(ctx), cols, B, ctx->log2B, ctx->structure, ctx->n, ctx->d_lam,
+                                      ctx->d_psi + g * tile, ctx->d_fpart, s);
+            RQ_LAUNCHED();
+            if (first) {
+                rq::launch_reduce_f(ctx->d_fpart, B, ctx->d_facc, s);
+                RQ_LAUNCHED();
+            }
+            if (!backward) continue;
+            for (int d = 0; d < kd; ++d) RQ_CUDA(cudaMemsetAsync(ctx->d_dlam + d * tile, 0, sizeof(double2) * tile, s));
+            const bool acc_env = want_env && first;
+            for (int l = g - 1; l >= 0; --l) {
+                const GateGeom &geo = ctx->geo[l];
+                rq::BwdArgs a;
+                a.lam = ctx->d_lam;
+                a.psi = ctx->d_psi + l * tile;
+                a.gate = ctx->d_gates + (long long)geo.param * 16;
+                a.geo = geo;
+                a.log2B = ctx->log2B;
+                a.tile_parity = par;
+                a.update = l > 0 ? 1 : 0;
+                a.n_items = (geo.mode == rq::kParity2 ? ctx->n_store / 2 : ctx->n_store / 4) * B;
+                for (int d = 0; d < kd; ++d) {
+                    rq::BwdArgs b = a;
+                    b.dlam = ctx->d_dlam + d * tile;
+                    b.dpsi = ctx->d_dpsi + d * set + l * tile;
+                    b.dir = ctx->d_dirs + ((long long)(d0 + d) * P + geo.param) * 16;
+                    b.accumulate = 1;
+                    b.part = ctx->d_partd + ((long long)d * g + l) * ctx->ncta * rq::kEnvDoubles;
+                    rq::launch_bwd_dir(b, ctx->ncta, s);
+                    RQ_LAUNCHED();
+                }
+                if (l > 0 || acc_env) {
+                    a.dlam = nullptr;
+                    a.dpsi = nullptr;
+                    a.dir = nullptr;
+                    a.accumulate = acc_env ? 1 : 0;
+                    a.part = ctx->d_part + (long long)l * ctx->ncta * rq::kEnvDoubles;
+                    rq::launch_bwd_base(a, ctx->ncta, s);
+                    RQ_LAUNCHED();
+                }
+            }
+            if (acc_env) {
+                rq::launch_reduce_env(ctx->d_part, ctx->ncta, g, ctx->d_env, s);
+                RQ_LAUNCHED();
+            }
+            for (int d = 0; d < kd; ++d) {
+                rq::launch_reduce_env(ctx->d_partd + (long long)d * g * ctx->ncta * rq::kEnvDoubles, ctx->ncta, g,
+                                      ctx->d_envd + (long long)(d0 + d) * g * rq::kEnvDoubles, s);
+                RQ_LAUNCHED();
+            }
+        }
+    }
+    rq::launch_geometry(ctx->d_gates, ctx->d_dirs, ctx->d_env, ctx->d_envd, ctx->d_param_of, g, P, k,
+                        ctx->structure, ctx->d_facc, f_out, want_env ? reinterpret_cast<double2 *>(rgrad) : nullptr,
+                        reinterpret_cast<double2 *>(hvps), s);
+    RQ_LAUNCHED();
+    return RQ_OK;
+}
+
+}  // namespace
+
+namespace rq {
+
+// Host-memory evaluation shared by the host entry points and the trust
+// region: inputs are copied in, outputs copied out, then the stream is
+// synchronised.
+rq_status eval_host(rq_ctx *ctx, const double *gates, const double *dirs, int k, int want_env, double *f,
+                    double *rgrad, double *hvps) {
+    if (!ctx) return RQ_EINVAL;
+    if (!ctx->ready) return fail(ctx, RQ_ESTATE, "no target set up (call rq_setup_target first)");
+    if (!gates) return fail(ctx, RQ_EINVAL, "gates is NULL");
+    if (k < 0) return fail(ctx, RQ_EINVAL, "k = %d < 0", k);
+    if (k > 0 && !dirs) return fail(ctx, RQ_EINVAL, "dirs is NULL with k = %d", k);
+    RQ_TRY(ensure_small(ctx, k));
+    cudaStream_t s = ctx->stream;
+    const long long gsz = (long long)ctx->P * 32;
+    RQ_CUDA(cudaMemcpyAsync(ctx->d_in_gates, gates, sizeof(double) * gsz, cudaMemcpyHostToDevice, s));
+    if (k > 0) RQ_CUDA(cudaMemcpyAsync(ctx->d_dirs_raw, dirs, sizeof(double) * gsz * k, cudaMemcpyHostToDevice, s));
+    double *o_f = ctx->d_out, *o_g = ctx->d_out + 1, *o_h = ctx->d_out + 1 + gsz;
+    RQ_TRY(eval_dev(ctx, reinterpret_cast<const double *>(ctx->d_in_gates),
+                    reinterpret_cast<const double *>(ctx->d_dirs_raw), k, want_env != 0, o_f, o_g, o_h));
+    if (f) RQ_CUDA(cudaMemcpyAsync(f, o_f, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (rgrad && want_env) RQ_CUDA(cudaMemcpyAsync(rgrad, o_g, sizeof(double) * gsz, cudaMemcpyDeviceToHost, s));
+    if (hvps && k > 0) RQ_CUDA(cudaMemcpyAsync(hvps, o_h, sizeof(double) * gsz * k, cudaMemcpyDeviceToHost, s));
+    RQ_CUDA(cudaStreamSynchronize(s));
+    return RQ_OK;
+}
+
+rq_status set_error(rq_ctx *ctx, rq_status code, const char *msg) { return fail(ctx, code, "%s", msg); }
+
+}  // namespace rq
+
+// ------------------------------------------------------------------ C ABI --
+
+extern "C" {
+
+rq_status rq_create(rq_ctx **out, int device, void *cuda_stream) {
+    if (!out) return fail(nullptr, RQ_EINVAL, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || device < 0 || device >= ndev)
+        return fail(nullptr, RQ_ECUDA, "device %d unavailable (%d devices): %s", device, ndev,
+                    cudaGetErrorString(e));
+    if ((e = cudaSetDevice(device)) != cudaSuccess)
+        return fail(nullptr, RQ_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    rq_ctx *ctx = new rq_ctx();
+    ctx->device = device;
+    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+    if (cuda_stream) {
+        ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+            delete ctx;
+            return fail(nullptr, RQ_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        }
+        ctx->own_stream = true;
+    }
+    *out = ctx;
+    return RQ_OK;
+}
+
+rq_status rq_destroy(rq_ctx *ctx) {
+    if (!ctx) return RQ_OK;
+    cudaSetDevice(ctx->device);
+    free_problem(ctx);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return RQ_OK;
+}
+
+rq_status rq_setup_target(rq_ctx *ctx, const rq_target *tgt, const rq_circuit *c) {
+    if (!ctx) return RQ_EINVAL;
+    if (!tgt || !c) return fail(ctx, RQ_EINVAL, "target or circuit is NULL");
+    if (tgt->model != 0) return fail(ctx, RQ_EINVAL, "model %d not supported (0: spinful Fermi-Hubbard)", tgt->model);
+    if (tgt->n_sites < 1 || 2 * tgt->n_sites != c->n_qubits || c->n_qubits > rq::kMaxQubits)
+        return fail(ctx, RQ_EINVAL, "n_qubits %d must equal 2 * n_sites (%d) and be <= %d", c->n_qubits,
+                    tgt->n_sites, rq::kMaxQubits);
+    if (!std::isfinite(tgt->J) || !std::isfinite(tgt->U) || !std::isfinite(tgt->t))
+        return fail(ctx, RQ_EINVAL, "J, U, t must be finite");
+    if (c->n_gates < 1 || !c->pairs) return fail(ctx, RQ_EINVAL, "circuit needs n_gates >= 1 and pairs");
+    if (c->structure != 0 && c->structure != 1) return fail(ctx, RQ_EINVAL, "structure must be 0 or 1");
+    const int P = c->param_of ? c->n_params : c->n_gates;
+    if (P < 1) return fail(ctx, RQ_EINVAL, "n_params must be >= 1");
+    for (int l = 0; l < c->n_gates; ++l) {
+        const int a = c->pairs[2 * l], b = c->pairs[2 * l + 1];
+        if (a < 0 || b < 0 || a >= c->n_qubits || b >= c->n_qubits || a == b)
+            return fail(ctx, RQ_EINVAL, "gate %d: invalid qubit pair (%d, %d)", l, a, b);
+        if (c->param_of && (c->param_of[l] < 0 || c->param_of[l] >= P))
+            return fail(ctx, RQ_EINVAL, "gate %d: param_of %d outside [0, %d)", l, c->param_of[l], P);
+    }
+    RQ_CUDA(cudaSetDevice(ctx->device));
+    free_problem(ctx);
+    ctx->tgt = *tgt;
+    ctx->n = c->n_qubits;
+    ctx->L = tgt->n_sites;
+    ctx->g = c->n_gates;
+    ctx->P = P;
+    ctx->structure = c->structure;
+    ctx->pairs.assign(c->pairs, c->pairs + 2 * ctx->g);
+    ctx->param_of.resize(ctx->g);
+    for (int l = 0; l < ctx->g; ++l) ctx->param_of[l] = c->param_of ? c->param_of[l] : l;
+    ctx->n_store = ctx->structure == 1 ? (1LL << (ctx->n - 1)) : (1LL << ctx->n);
+    ctx->geo.resize(ctx->g);
+    for (int l = 0; l < ctx->g; ++l) {
+        const int a = ctx->pairs[2 * l], b = ctx->pairs[2 * l + 1], n = ctx->n;
+        GateGeom &gg = ctx->geo[l];
+        gg.param = ctx->param_of[l];
+        gg.qfirst = 0;
+        if (ctx->structure == 0 || (a != 0 && b != 0)) {
+            gg.mode = ctx->structure == 0 ? rq::kGeneral : rq::kParity4;
+            gg.pa = n - 1 - a;
+            gg.pb = n - 1 - b;
+        } else {
+            const int q = a == 0 ? b : a;
+            gg.mode = rq::kParity2;
+            gg.pa = n - 1 - q;
+            gg.pb = -1;
+            gg.qfirst = a != 0 ? 1 : 0;
+        }
+    }
+    rq_status st = build_target(ctx);
+    if (st != RQ_OK) {
+        free_problem(ctx);
+        return st;
+    }
+    st = dev_alloc(ctx, &ctx->d_env, (long long)ctx->g * rq::kEnvDoubles, ctx->small_bytes);
+    if (st == RQ_OK) st = dev_alloc(ctx, &ctx->d_facc, 1, ctx->small_bytes);
+    if (st == RQ_OK) st = dev_alloc(ctx, &ctx->d_gates, (long long)P * 16, ctx->small_bytes);
+    if (st == RQ_OK) st = dev_alloc(ctx, &ctx->d_in_gates, (long long)P * 16, ctx->small_bytes);
+    if (st == RQ_OK) st = dev_alloc(ctx, &ctx->d_param_of, ctx->g, ctx->small_bytes);
+    if (st == RQ_OK &&
+        (cudaMemcpyAsync(ctx->d_param_of, ctx->param_of.data(), ctx->g * sizeof(int32_t), cudaMemcpyHostToDevice,
+                         ctx->stream) != cudaSuccess ||
+         cudaStreamSynchronize(ctx->stream) != cudaSuccess))
+        st = fail(ctx, RQ_ECUDA, "copy of param_of failed");
+    ctx->c0 = 0;
+    ctx->c1 = 1LL << ctx->n;
+    ctx->ready = true;
+    if (st == RQ_OK) st = ensure_small(ctx, 1);
+    if (st == RQ_OK) st = rebuild_tiles(ctx);
+    if (st != RQ_OK) free_problem(ctx);
+    return st;
+}
+
+rq_status rq_set_columns(rq_ctx *ctx, int64_t col_begin, int64_t col_end) {
+    if (!ctx) return RQ_EINVAL;
+    if (!ctx->ready) return fail(ctx, RQ_ESTATE, "no target set up");
+    if (col_begin < 0 || col_end < col_begin || col_end > (1LL << ctx->n))
+        return fail(ctx, RQ_EINVAL, "column range [%lld, %lld) outside [0, %lld)", (long long)col_begin,
+                    (long long)col_end, 1LL << ctx->n);
+    ctx->c0 = col_begin;
+    ctx->c1 = col_end;
+    return rebuild_tiles(ctx);
+}
+
+rq_status rq_set_tile(rq_ctx *ctx, int columns_per_tile, int max_dirs) {
+    if (!ctx) return RQ_EINVAL;
+    if (!ctx->ready) return fail(ctx, RQ_ESTATE, "no target set up");
+    if (columns_per_tile < 0 || (columns_per_tile & (columns_per_tile - 1)) != 0 || columns_per_tile > 65536)
+        return fail(ctx, RQ_EINVAL, "columns_per_tile %d is not 0 or a power of two <= 65536", columns_per_tile);
+    if (max_dirs < 0 || max_dirs > rq::kMaxDirs) return fail(ctx, RQ_EINVAL, "max_dirs %d outside [0, %d]", max_dirs, rq::kMaxDirs);
+    ctx->user_B = columns_per_tile;
+    ctx->user_kc = max_dirs;
+    return rebuild_tiles(ctx);
+}
+
+rq_status rq_cost(rq_ctx *ctx, const double *gates, double *f) {
+    if (!ctx) return RQ_EINVAL;
+    return rq::eval_host(ctx, gates, nullptr, 0, 0, f, nullptr, nullptr);
+}
+
+rq_status rq_grad(rq_ctx *ctx, const double *gates, double *f, double *rgrad) {
+    if (!ctx) return RQ_EINVAL;
+    return rq::eval_host(ctx, gates, nullptr, 0, 1, f, rgrad, nullptr);
+}
+
+rq_status rq_hvp(rq_ctx *ctx, const double *gates, const double *dirs, int k, double *f, double *rgrad,
+                 double *hvps) {
+    if (!ctx) return RQ_EINVAL;
+    return rq::eval_host(ctx, gates, dirs, k, 1, f, rgrad, hvps);
+}
+
+rq_status rq_cost_dev(rq_ctx *ctx, const double *gates, double *f) {
+    if (!ctx) return RQ_EINVAL;
+    return eval_dev(ctx, gates, nullptr, 0, false, f, nullptr, nullptr);
+}
+
+rq_status rq_grad_dev(rq_ctx *ctx, const double *gates, double *f, double *rgrad) {
+    if (!ctx) return RQ_EINVAL;
+    return eval_dev(ctx, gates, nullptr, 0, true, f, rgrad, nullptr);
+}
+
+rq_status rq_hvp_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, double *f, double *rgrad,
+                     double *hvps) {
+    if (!ctx) return RQ_EINVAL;
+    return eval_dev(ctx, gates, dirs, k, true, f, rgrad, hvps);
+}
+
+rq_status rq_target_column(rq_ctx *ctx, int64_t j, double *out) {
+    if (!ctx) return RQ_EINVAL;
+    if (!ctx->ready) return fail(ctx, RQ_ESTATE, "no target set up");
+    if (!out || j < 0 || j >= (1LL << ctx->n)) return fail(ctx, RQ_EINVAL, "invalid column %lld", (long long)j);
+    const int s = ctx->sec_of_h[j];
+    const long long m = ctx->off_basis[s + 1] - ctx->off_basis[s];
+    std::vector<double2> col(m);
+    RQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    RQ_CUDA(cudaMemcpyAsync(col.data(), ctx->d_U + ctx->off_u[s] + (long long)ctx->pos_h[j] * m, m * sizeof(double2),
+                            cudaMemcpyDeviceToHost, ctx->stream));
+    RQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    std::memset(out, 0, sizeof(double) * 2 * (1LL << ctx->n));
+    for (long long r = 0; r < m; ++r) {
+        const long long x = ctx->basis_h[ctx->off_basis[s] + r];
+        out[2 * x] = col[r].x;
+        out[2 * x + 1] = col[r].y;
+    }
+    return RQ_OK;
+}
+
+rq_status rq_get_info(const rq_ctx *ctx, rq_info_t *info) {
+    if (!ctx || !info) return RQ_EINVAL;
+    std::memset(info, 0, sizeof(*info));
+    info->kernel_launches = ctx->launches;
+    if (!ctx->ready) return RQ_OK;
+    info->n_qubits = ctx->n;
+    info->n_gates = ctx->g;
+    info->n_params = ctx->P;
+    info->structure = ctx->structure;
+    info->amplitudes_per_column = ctx->n_store;
+    info->columns = ctx->c1 - ctx->c0;
+    info->columns_per_tile = ctx->B;
+    info->n_tiles = ctx->n_tiles;
+    info->max_dirs = ctx->kc;
+    info->workspace_bytes = ctx->problem_bytes + ctx->work_bytes + ctx->small_bytes;
+    info->target_entries = ctx->u_entries;
+    return RQ_OK;
+}
+
+const char *rq_last_error(const rq_ctx *ctx) {
+    if (!ctx) return g_create_error.c_str();
+    return ctx->err.c_str();
+}
+
+}  // extern "C"

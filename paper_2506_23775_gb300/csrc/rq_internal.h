@@ -1,0 +1,117 @@
+// Internal declarations of the rq library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/rq.h"
+
+namespace rq {
+
+constexpr int kThreads = 256;      // threads per CTA of every sweep kernel
+constexpr int kCtasPerSm = 2;      // sweep CTAs launched per SM (grid size)
+constexpr int kMaxDirs = 4;        // HVP directions swept together
+constexpr int kMaxQubits = 20;
+constexpr int kEnvDoubles = 32;    // one 4x4 complex environment
+
+// Which kernel family handles a gate.
+enum GateMode : int {
+    kGeneral = 0,     // general 4x4 gate, full 2^n layout
+    kParity4 = 1,     // parity gate on two stored qubits (two 2x2 blocks)
+    kParity2 = 2,     // parity gate touching the implied qubit (one 2x2 block per item)
+};
+
+struct GateGeom {
+    int mode;      // GateMode
+    int pa, pb;    // stored bit positions of the listed qubits (kParity2: pa = other qubit, pb = -1)
+    int qfirst;    // kParity2: 1 if the stored qubit is listed first
+    int param;     // parameter gate index
+};
+
+// Arguments of one forward gate step over a tile.
+struct FwdArgs {
+    const double2 *psi_in;
+    double2 *psi_out;
+    const double2 *dpsi_in;     // direction 0; direction d at + d * dir_stride
+    double2 *dpsi_out;
+    long long dir_stride;       // elements between directions' checkpoint sets
+    int kdirs;
+    const double2 *gate;        // 16 entries
+    const double2 *dirs;        // direction 0 of this parameter; direction d at + d * xdir_stride
+    long long xdir_stride;
+    GateGeom geo;
+    int log2B;
+    int tile_parity;
+    long long n_items;
+};
+
+// Arguments of one backward gate step over a tile.
+struct BwdArgs {
+    double2 *lam;               // lambda_l, updated in place to lambda_{l-1} (base step)
+    double2 *dlam;              // direction step: lambda-dot_l, updated in place
+    const double2 *psi;         // psi_{l-1}
+    const double2 *dpsi;        // psi-dot_{l-1} (direction step)
+    const double2 *gate;
+    const double2 *dir;         // X of this parameter for the direction (direction step)
+    GateGeom geo;
+    int log2B;
+    int tile_parity;
+    int update;                 // 0: skip the state update (first gate)
+    int accumulate;             // base step: 0 skips the environment (and part)
+    long long n_items;
+    double *part;               // [gridDim.x][32] per-CTA partial environments
+};
+
+// Sector tables of the stored target.
+struct TargetDev {
+    const int32_t *sec_of;      // [2^n] sector id of a basis index
+    const int32_t *pos;         // [2^n] position inside its sector
+    const int32_t *basis;       // concatenated ascending basis lists
+    const long long *off_basis; // [S+1]
+    const long long *off_u;     // [S+1] offsets of the column-major U blocks
+    const double2 *U;
+};
+
+// Launchers (rq_sweep.cu).
+void launch_fwd(const FwdArgs &a, int grid, cudaStream_t s);
+void launch_bwd_base(const BwdArgs &a, int grid, cudaStream_t s);
+void launch_bwd_dir(const BwdArgs &a, int grid, cudaStream_t s);
+void launch_init_unit(double2 *psi0, const int32_t *cols, int B, int log2B, long long n_store,
+                      int parity_layout, cudaStream_t s);
+
+// Launchers (rq_target.cu).
+void launch_scatter_target(const TargetDev &t, const int32_t *cols, int B, int log2B,
+                           int parity_layout, int n, double2 *lam, const double2 *psi_final,
+                           double *fpart, cudaStream_t s);
+void launch_cheb_step(const TargetDev &t, int n_sectors, long long total, const double *cur,
+                      double *prev_out, double2 *acc, double2 coef, double scale, int first,
+                      double diag_scale, double diag_shift, double hop_scale,
+                      const long long *bond_masks, int n_bonds, int L, double U, cudaStream_t s);
+void launch_cheb_init(const long long *off_u, const long long *sizes, int n_sectors, long long total,
+                      double *prev, double2 *acc, double2 c0, cudaStream_t s);
+
+// Launchers (rq_geometry.cu).
+void launch_reduce_env(const double *part, int ncta, int n_gates, double *env, cudaStream_t s);
+void launch_reduce_f(const double *fpart, int B, double *facc, cudaStream_t s);
+void launch_project_dirs(const double2 *gates, const double2 *raw, double2 *out, int n_params,
+                         int k, int structure, cudaStream_t s);
+void launch_mask_gates(const double2 *in, double2 *out, int n_params, int structure, cudaStream_t s);
+void launch_geometry(const double2 *gates, const double2 *dirs, const double *env,
+                     const double *env_dot, const int32_t *param_of, int n_gates, int n_params,
+                     int k, int structure, const double *facc, double *f_out, double2 *rgrad,
+                     double2 *hvps, cudaStream_t s);
+
+// Host-memory evaluation (rq_api.cu): copies inputs in and outputs out and
+// synchronises; want_env = 0 skips the gradient environments.
+rq_status eval_host(rq_ctx *ctx, const double *gates, const double *dirs, int k, int want_env, double *f,
+                    double *rgrad, double *hvps);
+rq_status set_error(rq_ctx *ctx, rq_status code, const char *msg);
+
+// Host helpers.
+int polar_unitary_4x4(const double *A, double *Q);    // rq_tr.cpp; 32 doubles in/out, 0 on success
+double bessel_j_table(double x, int kmax, std::vector<double> &out);  // rq_target.cu; J_0..J_kmax(x)
+
+}  // namespace rq

@@ -1,0 +1,461 @@
+// Gate sweeps over a tile of basis columns: forward (with tangents) and
+// backward (adjoint states with gate-hole environments).
+//
+// Layout: a tile is [amplitudes x B columns] complex128 with the column index
+// fastest, so the four amplitudes a gate mixes are four coalesced rows of B
+// columns whatever the qubit pair (the paper's "locally sequential streams"
+// of Sec. "Gate application" become full-width coalesced warps here).
+//
+// * Forward (Fig. forward_pass; Eq. gate_application_neighboring and its
+//   general five-leg form): psi_{l+1} = G_l psi_l, and for each HVP direction
+//   the forward-mode tangent psi'_{l+1} = G_l psi'_l + X_l psi_l (Appendix
+//   "Evaluating Hessian-vector products").
+// * Backward (Fig. backward_pass_gate_gradient, Fig. hole_contraction): the
+//   paper propagates phi = (U|j>)^* with transposed gates and contracts the
+//   gate hole y (x) x; here the adjoint state is kept as the ket
+//   lambda = conj(phi), propagated with G^dagger, and the hole is
+//   E[a][c] += conj(lambda[a]) psi[c].  The direction step adds
+//   E'[a][c] += conj(lambda'[a]) psi[c] + conj(lambda[a]) psi'[c] and
+//   lambda' <- G^dagger lambda' + X^dagger lambda (reverse pass over the
+//   directed-gradient graph, Fig. directed_gradient_graph).
+// * Parity-conserving gates (Eq. paritygatematrix) keep each column in its
+//   parity sector, so a tile of equal-parity columns stores 2^(n-1)
+//   amplitudes: qubit 0 is implied by the parity of the stored bits.  A gate
+//   away from qubit 0 acts as its two 2x2 blocks on four stored amplitudes; a
+//   gate on qubit 0 acts as one 2x2 block on two stored amplitudes, the block
+//   chosen by the parity of the other stored bits.
+//
+// Environments are accumulated per thread in FP64 registers, reduced with a
+// fixed warp-shuffle tree and a fixed-order block sum into one partial per
+// CTA; a later kernel sums the partials in CTA order (deterministic).
+#include "rq_internal.h"
+
+namespace rq {
+namespace {
+
+__device__ __forceinline__ long long insert_zero(long long r, int p) {
+    const long long lo = r & ((1LL << p) - 1);
+    return ((r >> p) << (p + 1)) | lo;
+}
+
+// acc += a * b
+__device__ __forceinline__ void cmac(double2 &acc, const double2 a, const double2 b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+
+// acc += conj(a) * b
+__device__ __forceinline__ void cmacc(double2 &acc, const double2 a, const double2 b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+}
+
+__device__ __forceinline__ double2 zero2() { return make_double2(0.0, 0.0); }
+
+// Stored offsets of the four amplitudes of item (r, b) for a gate on the
+// listed pair with stored bit positions pa (first listed) and pb.
+__device__ __forceinline__ void offsets4(long long r, long long b, int pa, int pb, int log2B,
+                                         long long (&off)[4]) {
+    const int plo = pa < pb ? pa : pb;
+    const int phi = pa < pb ? pb : pa;
+    const long long x0 = insert_zero(insert_zero(r, plo), phi);
+    const long long sa = 1LL << pa, sb = 1LL << pb;
+    off[0] = (x0 << log2B) | b;
+    off[1] = ((x0 | sb) << log2B) | b;
+    off[2] = ((x0 | sa) << log2B) | b;
+    off[3] = ((x0 | sa | sb) << log2B) | b;
+}
+
+// kParity2 item: the two stored amplitudes differ in the stored qubit at
+// bit p; e = bit of the implied qubit for the first one.  Returns the local
+// 4x4 indices (i0, i1) of the two amplitudes.
+__device__ __forceinline__ void offsets2(long long r, long long b, int p, int qfirst, int parity,
+                                         int log2B, long long (&off)[2], int &i0, int &i1) {
+    const long long y0 = insert_zero(r, p);
+    off[0] = (y0 << log2B) | b;
+    off[1] = ((y0 | (1LL << p)) << log2B) | b;
+    const int e = (__popcll(y0) & 1) ^ parity;
+    if (e == 0) {
+        i0 = 0;
+        i1 = 3;
+    } else if (qfirst) {
+        i0 = 1;
+        i1 = 2;
+    } else {
+        i0 = 2;
+        i1 = 1;
+    }
+}
+
+// ---------------------------------------------------------------- forward --
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) k_fwd(const FwdArgs a) {
+    __shared__ double2 sg[16];
+    __shared__ double2 sx[kMaxDirs][16];
+    if (threadIdx.x < 16) sg[threadIdx.x] = a.gate[threadIdx.x];
+    if (threadIdx.x < 16 * a.kdirs)
+        sx[threadIdx.x >> 4][threadIdx.x & 15] = a.dirs[(threadIdx.x >> 4) * a.xdir_stride + (threadIdx.x & 15)];
+    __syncthreads();
+    const long long Bm = (1LL << a.log2B) - 1;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.n_items; it += stride) {
+        const long long b = it & Bm, r = it >> a.log2B;
+        if (MODE == kGeneral || MODE == kParity4) {
+            long long off[4];
+            offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
+            double2 p[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) p[c] = __ldg(&a.psi_in[off[c]]);
+            double2 q[4];
+            if (MODE == kGeneral) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    q[i] = zero2();
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) cmac(q[i], sg[i * 4 + c], p[c]);
+                }
+            } else {
+                q[0] = zero2(); cmac(q[0], sg[0], p[0]); cmac(q[0], sg[3], p[3]);
+                q[3] = zero2(); cmac(q[3], sg[12], p[0]); cmac(q[3], sg[15], p[3]);
+                q[1] = zero2(); cmac(q[1], sg[5], p[1]); cmac(q[1], sg[6], p[2]);
+                q[2] = zero2(); cmac(q[2], sg[9], p[1]); cmac(q[2], sg[10], p[2]);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) a.psi_out[off[c]] = q[c];
+            for (int d = 0; d < a.kdirs; ++d) {
+                const double2 *din = a.dpsi_in + d * a.dir_stride;
+                double2 *dout = a.dpsi_out + d * a.dir_stride;
+                double2 t[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) t[c] = __ldg(&din[off[c]]);
+                if (MODE == kGeneral) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        q[i] = zero2();
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            cmac(q[i], sg[i * 4 + c], t[c]);
+                            cmac(q[i], sx[d][i * 4 + c], p[c]);
+                        }
+                    }
+                } else {
+                    const int E0[2] = {0, 3}, O0[2] = {1, 2};
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int i = E0[u];
+                        q[i] = zero2();
+                        cmac(q[i], sg[i * 4 + 0], t[0]); cmac(q[i], sg[i * 4 + 3], t[3]);
+                        cmac(q[i], sx[d][i * 4 + 0], p[0]); cmac(q[i], sx[d][i * 4 + 3], p[3]);
+                        const int o = O0[u];
+                        q[o] = zero2();
+                        cmac(q[o], sg[o * 4 + 1], t[1]); cmac(q[o], sg[o * 4 + 2], t[2]);
+                        cmac(q[o], sx[d][o * 4 + 1], p[1]); cmac(q[o], sx[d][o * 4 + 2], p[2]);
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) dout[off[c]] = q[c];
+            }
+        } else {  // kParity2
+            long long off[2];
+            int i0, i1;
+            offsets2(r, b, a.geo.pa, a.geo.qfirst, a.tile_parity, a.log2B, off, i0, i1);
+            const double2 p0 = __ldg(&a.psi_in[off[0]]), p1 = __ldg(&a.psi_in[off[1]]);
+            double2 q0 = zero2(), q1 = zero2();
+            cmac(q0, sg[i0 * 4 + i0], p0); cmac(q0, sg[i0 * 4 + i1], p1);
+            cmac(q1, sg[i1 * 4 + i0], p0); cmac(q1, sg[i1 * 4 + i1], p1);
+            a.psi_out[off[0]] = q0;
+            a.psi_out[off[1]] = q1;
+            for (int d = 0; d < a.kdirs; ++d) {
+                const double2 *din = a.dpsi_in + d * a.dir_stride;
+                double2 *dout = a.dpsi_out + d * a.dir_stride;
+                const double2 t0 = __ldg(&din[off[0]]), t1 = __ldg(&din[off[1]]);
+                q0 = zero2();
+                q1 = zero2();
+                cmac(q0, sg[i0 * 4 + i0], t0); cmac(q0, sg[i0 * 4 + i1], t1);
+                cmac(q1, sg[i1 * 4 + i0], t0); cmac(q1, sg[i1 * 4 + i1], t1);
+                cmac(q0, sx[d][i0 * 4 + i0], p0); cmac(q0, sx[d][i0 * 4 + i1], p1);
+                cmac(q1, sx[d][i1 * 4 + i0], p0); cmac(q1, sx[d][i1 * 4 + i1], p1);
+                dout[off[0]] = q0;
+                dout[off[1]] = q1;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------- block reduction --
+
+// Sum acc over the CTA in a fixed order and store 32 doubles at out.
+__device__ __forceinline__ void block_reduce_store(const double2 (&acc)[16], double *out) {
+    __shared__ double red[kThreads / 32][kEnvDoubles];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        double vx = acc[i].x, vy = acc[i].y;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            vx += __shfl_xor_sync(0xffffffffu, vx, o);
+            vy += __shfl_xor_sync(0xffffffffu, vy, o);
+        }
+        if (lane == 0) {
+            red[warp][2 * i] = vx;
+            red[warp][2 * i + 1] = vy;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kEnvDoubles) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) s += red[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------- backward base --
+
+// E[a][c] += conj(lambda[a]) psi[c]; lambda <- G^dagger lambda.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) k_bwd_base(const BwdArgs a) {
+    const int accumulate = a.accumulate;
+    __shared__ double2 sg[16];
+    if (threadIdx.x < 16) sg[threadIdx.x] = a.gate[threadIdx.x];
+    __syncthreads();
+    double2 E[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) E[i] = zero2();
+    const long long Bm = (1LL << a.log2B) - 1;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.n_items; it += stride) {
+        const long long b = it & Bm, r = it >> a.log2B;
+        if (MODE == kGeneral || MODE == kParity4) {
+            long long off[4];
+            offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
+            double2 l[4], p[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                l[c] = a.lam[off[c]];
+                p[c] = __ldg(&a.psi[off[c]]);
+            }
+            if (accumulate) {
+                if (MODE == kGeneral) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) cmacc(E[i * 4 + c], l[i], p[c]);
+                } else {
+                    cmacc(E[0], l[0], p[0]); cmacc(E[3], l[0], p[3]);
+                    cmacc(E[12], l[3], p[0]); cmacc(E[15], l[3], p[3]);
+                    cmacc(E[5], l[1], p[1]); cmacc(E[6], l[1], p[2]);
+                    cmacc(E[9], l[2], p[1]); cmacc(E[10], l[2], p[2]);
+                }
+            }
+            if (a.update) {
+                double2 q[4];
+                if (MODE == kGeneral) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        q[i] = zero2();
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) cmacc(q[i], sg[c * 4 + i], l[c]);
+                    }
+                } else {
+                    q[0] = zero2(); cmacc(q[0], sg[0], l[0]); cmacc(q[0], sg[12], l[3]);
+                    q[3] = zero2(); cmacc(q[3], sg[3], l[0]); cmacc(q[3], sg[15], l[3]);
+                    q[1] = zero2(); cmacc(q[1], sg[5], l[1]); cmacc(q[1], sg[9], l[2]);
+                    q[2] = zero2(); cmacc(q[2], sg[6], l[1]); cmacc(q[2], sg[10], l[2]);
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) a.lam[off[c]] = q[c];
+            }
+        } else {  // kParity2
+            long long off[2];
+            int i0, i1;
+            offsets2(r, b, a.geo.pa, a.geo.qfirst, a.tile_parity, a.log2B, off, i0, i1);
+            const double2 l0 = a.lam[off[0]], l1 = a.lam[off[1]];
+            if (accumulate) {
+                const double2 p0 = __ldg(&a.psi[off[0]]), p1 = __ldg(&a.psi[off[1]]);
+                // E[i0][i0], E[i0][i1], E[i1][i0], E[i1][i1]; written with
+                // static indices per block so the accumulators stay in registers
+                double2 c00 = zero2(), c01 = zero2(), c10 = zero2(), c11 = zero2();
+                cmacc(c00, l0, p0); cmacc(c01, l0, p1); cmacc(c10, l1, p0); cmacc(c11, l1, p1);
+                if (i0 == 0) {
+                    E[0].x += c00.x; E[0].y += c00.y; E[3].x += c01.x; E[3].y += c01.y;
+                    E[12].x += c10.x; E[12].y += c10.y; E[15].x += c11.x; E[15].y += c11.y;
+                } else if (i0 == 1) {
+                    E[5].x += c00.x; E[5].y += c00.y; E[6].x += c01.x; E[6].y += c01.y;
+                    E[9].x += c10.x; E[9].y += c10.y; E[10].x += c11.x; E[10].y += c11.y;
+                } else {
+                    E[10].x += c00.x; E[10].y += c00.y; E[9].x += c01.x; E[9].y += c01.y;
+                    E[6].x += c10.x; E[6].y += c10.y; E[5].x += c11.x; E[5].y += c11.y;
+                }
+            }
+            if (a.update) {
+                double2 q0 = zero2(), q1 = zero2();
+                cmacc(q0, sg[i0 * 4 + i0], l0); cmacc(q0, sg[i1 * 4 + i0], l1);
+                cmacc(q1, sg[i0 * 4 + i1], l0); cmacc(q1, sg[i1 * 4 + i1], l1);
+                a.lam[off[0]] = q0;
+                a.lam[off[1]] = q1;
+            }
+        }
+    }
+    if (accumulate) block_reduce_store(E, a.part + (long long)blockIdx.x * kEnvDoubles);
+}
+
+// ----------------------------------------------------- backward direction --
+
+// E'[a][c] += conj(lambda'[a]) psi[c] + conj(lambda[a]) psi'[c];
+// lambda' <- G^dagger lambda' + X^dagger lambda.  Runs before the base step
+// of the same gate (it reads lambda_l before that step overwrites it).
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) k_bwd_dir(const BwdArgs a) {
+    __shared__ double2 sg[16];
+    __shared__ double2 sx[16];
+    if (threadIdx.x < 16) {
+        sg[threadIdx.x] = a.gate[threadIdx.x];
+        sx[threadIdx.x] = a.dir[threadIdx.x];
+    }
+    __syncthreads();
+    double2 E[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) E[i] = zero2();
+    const long long Bm = (1LL << a.log2B) - 1;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.n_items; it += stride) {
+        const long long b = it & Bm, r = it >> a.log2B;
+        if (MODE == kGeneral || MODE == kParity4) {
+            long long off[4];
+            offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
+            double2 l[4], dl[4], p[4], dp[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                l[c] = __ldg(&a.lam[off[c]]);
+                dl[c] = a.dlam[off[c]];
+                p[c] = __ldg(&a.psi[off[c]]);
+                dp[c] = __ldg(&a.dpsi[off[c]]);
+            }
+            if (MODE == kGeneral) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        cmacc(E[i * 4 + c], dl[i], p[c]);
+                        cmacc(E[i * 4 + c], l[i], dp[c]);
+                    }
+            } else {
+                const int idx[8][2] = {{0, 0}, {0, 3}, {3, 0}, {3, 3}, {1, 1}, {1, 2}, {2, 1}, {2, 2}};
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    cmacc(E[idx[u][0] * 4 + idx[u][1]], dl[idx[u][0]], p[idx[u][1]]);
+                    cmacc(E[idx[u][0] * 4 + idx[u][1]], l[idx[u][0]], dp[idx[u][1]]);
+                }
+            }
+            if (a.update) {
+                double2 q[4];
+                if (MODE == kGeneral) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        q[i] = zero2();
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            cmacc(q[i], sg[c * 4 + i], dl[c]);
+                            cmacc(q[i], sx[c * 4 + i], l[c]);
+                        }
+                    }
+                } else {
+                    q[0] = zero2(); cmacc(q[0], sg[0], dl[0]); cmacc(q[0], sg[12], dl[3]);
+                    cmacc(q[0], sx[0], l[0]); cmacc(q[0], sx[12], l[3]);
+                    q[3] = zero2(); cmacc(q[3], sg[3], dl[0]); cmacc(q[3], sg[15], dl[3]);
+                    cmacc(q[3], sx[3], l[0]); cmacc(q[3], sx[15], l[3]);
+                    q[1] = zero2(); cmacc(q[1], sg[5], dl[1]); cmacc(q[1], sg[9], dl[2]);
+                    cmacc(q[1], sx[5], l[1]); cmacc(q[1], sx[9], l[2]);
+                    q[2] = zero2(); cmacc(q[2], sg[6], dl[1]); cmacc(q[2], sg[10], dl[2]);
+                    cmacc(q[2], sx[6], l[1]); cmacc(q[2], sx[10], l[2]);
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) a.dlam[off[c]] = q[c];
+            }
+        } else {  // kParity2
+            long long off[2];
+            int i0, i1;
+            offsets2(r, b, a.geo.pa, a.geo.qfirst, a.tile_parity, a.log2B, off, i0, i1);
+            const double2 l0 = __ldg(&a.lam[off[0]]), l1 = __ldg(&a.lam[off[1]]);
+            const double2 d0 = a.dlam[off[0]], d1 = a.dlam[off[1]];
+            const double2 p0 = __ldg(&a.psi[off[0]]), p1 = __ldg(&a.psi[off[1]]);
+            const double2 t0 = __ldg(&a.dpsi[off[0]]), t1 = __ldg(&a.dpsi[off[1]]);
+            double2 c00 = zero2(), c01 = zero2(), c10 = zero2(), c11 = zero2();
+            cmacc(c00, d0, p0); cmacc(c00, l0, t0);
+            cmacc(c01, d0, p1); cmacc(c01, l0, t1);
+            cmacc(c10, d1, p0); cmacc(c10, l1, t0);
+            cmacc(c11, d1, p1); cmacc(c11, l1, t1);
+            if (i0 == 0) {
+                E[0].x += c00.x; E[0].y += c00.y; E[3].x += c01.x; E[3].y += c01.y;
+                E[12].x += c10.x; E[12].y += c10.y; E[15].x += c11.x; E[15].y += c11.y;
+            } else if (i0 == 1) {
+                E[5].x += c00.x; E[5].y += c00.y; E[6].x += c01.x; E[6].y += c01.y;
+                E[9].x += c10.x; E[9].y += c10.y; E[10].x += c11.x; E[10].y += c11.y;
+            } else {
+                E[10].x += c00.x; E[10].y += c00.y; E[9].x += c01.x; E[9].y += c01.y;
+                E[6].x += c10.x; E[6].y += c10.y; E[5].x += c11.x; E[5].y += c11.y;
+            }
+            if (a.update) {
+                double2 q0 = zero2(), q1 = zero2();
+                cmacc(q0, sg[i0 * 4 + i0], d0); cmacc(q0, sg[i1 * 4 + i0], d1);
+                cmacc(q0, sx[i0 * 4 + i0], l0); cmacc(q0, sx[i1 * 4 + i0], l1);
+                cmacc(q1, sg[i0 * 4 + i1], d0); cmacc(q1, sg[i1 * 4 + i1], d1);
+                cmacc(q1, sx[i0 * 4 + i1], l0); cmacc(q1, sx[i1 * 4 + i1], l1);
+                a.dlam[off[0]] = q0;
+                a.dlam[off[1]] = q1;
+            }
+        }
+    }
+    block_reduce_store(E, a.part + (long long)blockIdx.x * kEnvDoubles);
+}
+
+// psi_0 = |j_b> for every column b of the tile (the tile is zeroed before).
+__global__ void k_init_unit(double2 *psi0, const int32_t *cols, int B, int log2B, long long mask) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const int j = cols[b];
+    if (j < 0) return;
+    const long long y = (long long)j & mask;
+    psi0[(y << log2B) | b] = make_double2(1.0, 0.0);
+}
+
+}  // namespace
+
+void launch_fwd(const FwdArgs &a, int grid, cudaStream_t s) {
+    switch (a.geo.mode) {
+        case kGeneral: k_fwd<kGeneral><<<grid, kThreads, 0, s>>>(a); break;
+        case kParity4: k_fwd<kParity4><<<grid, kThreads, 0, s>>>(a); break;
+        default: k_fwd<kParity2><<<grid, kThreads, 0, s>>>(a); break;
+    }
+}
+
+void launch_bwd_base(const BwdArgs &a, int grid, cudaStream_t s) {
+    switch (a.geo.mode) {
+        case kGeneral: k_bwd_base<kGeneral><<<grid, kThreads, 0, s>>>(a); break;
+        case kParity4: k_bwd_base<kParity4><<<grid, kThreads, 0, s>>>(a); break;
+        default: k_bwd_base<kParity2><<<grid, kThreads, 0, s>>>(a); break;
+    }
+}
+
+void launch_bwd_dir(const BwdArgs &a, int grid, cudaStream_t s) {
+    switch (a.geo.mode) {
+        case kGeneral: k_bwd_dir<kGeneral><<<grid, kThreads, 0, s>>>(a); break;
+        case kParity4: k_bwd_dir<kParity4><<<grid, kThreads, 0, s>>>(a); break;
+        default: k_bwd_dir<kParity2><<<grid, kThreads, 0, s>>>(a); break;
+    }
+}
+
+void launch_init_unit(double2 *psi0, const int32_t *cols, int B, int log2B, long long n_store,
+                      int parity_layout, cudaStream_t s) {
+    const long long mask = n_store - 1;  // drops the implied top qubit in the parity layout
+    (void)parity_layout;
+    k_init_unit<<<(B + 127) / 128, 128, 0, s>>>(psi0, cols, B, log2B, mask);
+}
+
+}  // namespace rq

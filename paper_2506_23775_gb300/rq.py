@@ -1,0 +1,231 @@
+"""Thin ctypes binding of the ``rq`` C ABI (``include/rq.h``).
+
+Argument marshalling only: every step of the cost, gradient, HVP and
+trust-region computation runs inside ``librq.so`` on the GPU.  Importing this
+module does not load the library; the first :class:`Context` does, and it
+raises if the library is missing (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+
+_LIB = None
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "librq.so")
+
+RQ_OK, RQ_EINVAL, RQ_ENOMEM, RQ_ECUDA, RQ_ETIMEOUT, RQ_ESTATE = 0, -1, -2, -3, -4, -5
+
+# Every symbol declared in include/rq.h.
+EXPORTS = ("rq_create", "rq_destroy", "rq_setup_target", "rq_set_columns", "rq_set_tile",
+           "rq_cost", "rq_grad", "rq_hvp", "rq_cost_dev", "rq_grad_dev", "rq_hvp_dev",
+           "rq_tr_step", "rq_target_column", "rq_get_info", "rq_last_error")
+
+
+class RQCircuit(C.Structure):
+    _fields_ = [("n_qubits", C.c_int), ("n_gates", C.c_int), ("n_params", C.c_int),
+                ("structure", C.c_int), ("pairs", C.POINTER(C.c_int32)),
+                ("param_of", C.POINTER(C.c_int32))]
+
+
+class RQTarget(C.Structure):
+    _fields_ = [("model", C.c_int), ("n_sites", C.c_int), ("periodic", C.c_int),
+                ("J", C.c_double), ("U", C.c_double), ("t", C.c_double)]
+
+
+class RQTRState(C.Structure):
+    _fields_ = [("radius", C.c_double), ("max_radius", C.c_double), ("rho_accept", C.c_double),
+                ("kappa", C.c_double), ("theta", C.c_double), ("max_inner", C.c_int),
+                ("f", C.c_double), ("f_new", C.c_double), ("rho", C.c_double),
+                ("grad_norm", C.c_double), ("step_norm", C.c_double), ("accepted", C.c_int),
+                ("n_inner", C.c_int), ("tcg_exit", C.c_int)]
+
+
+class RQInfo(C.Structure):
+    _fields_ = [("n_qubits", C.c_int), ("n_gates", C.c_int), ("n_params", C.c_int),
+                ("structure", C.c_int), ("amplitudes_per_column", C.c_int64),
+                ("columns", C.c_int64), ("columns_per_tile", C.c_int), ("n_tiles", C.c_int),
+                ("max_dirs", C.c_int), ("workspace_bytes", C.c_int64),
+                ("target_entries", C.c_int64), ("kernel_launches", C.c_int64)]
+
+
+class RQError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rq error {code}: {msg}")
+        self.code = code
+
+
+def load(path: Optional[str] = None) -> C.CDLL:
+    """Load ``librq.so`` (raises ``OSError`` if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise OSError(f"{path} not found: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(path)
+    vp, dp, i64 = C.c_void_p, C.POINTER(C.c_double), C.c_int64
+    sig = {
+        "rq_create": ([C.POINTER(vp), C.c_int, vp], C.c_int),
+        "rq_destroy": ([vp], C.c_int),
+        "rq_setup_target": ([vp, C.POINTER(RQTarget), C.POINTER(RQCircuit)], C.c_int),
+        "rq_set_columns": ([vp, i64, i64], C.c_int),
+        "rq_set_tile": ([vp, C.c_int, C.c_int], C.c_int),
+        "rq_cost": ([vp, dp, dp], C.c_int),
+        "rq_grad": ([vp, dp, dp, dp], C.c_int),
+        "rq_hvp": ([vp, dp, dp, C.c_int, dp, dp, dp], C.c_int),
+        "rq_cost_dev": ([vp, vp, vp], C.c_int),
+        "rq_grad_dev": ([vp, vp, vp, vp], C.c_int),
+        "rq_hvp_dev": ([vp, vp, vp, C.c_int, vp, vp, vp], C.c_int),
+        "rq_tr_step": ([vp, dp, C.POINTER(RQTRState)], C.c_int),
+        "rq_target_column": ([vp, i64, dp], C.c_int),
+        "rq_get_info": ([vp, C.POINTER(RQInfo)], C.c_int),
+        "rq_last_error": ([vp], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _LIB = lib
+    return lib
+
+
+def _dptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _c128(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+class Context:
+    """One device context: a target, a circuit and a column range."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None):
+        self._lib = load()
+        h = C.c_void_p()
+        st = self._lib.rq_create(C.byref(h), device, C.c_void_p(stream) if stream else None)
+        if st != RQ_OK:
+            raise RQError(st, self._lib.rq_last_error(None).decode())
+        self._h = h
+        self.n_params = 0
+        self.n_qubits = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rq_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st: int):
+        if st != RQ_OK:
+            raise RQError(st, self._lib.rq_last_error(self._h).decode())
+
+    # --- set-up ---------------------------------------------------------
+    def setup(self, n_sites: int, pairs, param_of=None, n_params: Optional[int] = None,
+              structure: int = 0, J: float = 1.0, U: float = 4.0, t: float = 0.5,
+              periodic: bool = False):
+        pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+        self._pairs = pairs
+        if param_of is not None:
+            self._param_of = np.ascontiguousarray(param_of, dtype=np.int32)
+            npar = int(n_params if n_params is not None else self._param_of.max() + 1)
+            pp = self._param_of.ctypes.data_as(C.POINTER(C.c_int32))
+        else:
+            self._param_of = None
+            npar = pairs.shape[0]
+            pp = None
+        circ = RQCircuit(2 * n_sites, pairs.shape[0], npar, structure,
+                         pairs.ctypes.data_as(C.POINTER(C.c_int32)), pp)
+        tgt = RQTarget(0, n_sites, 1 if periodic else 0, J, U, t)
+        self._check(self._lib.rq_setup_target(self._h, C.byref(tgt), C.byref(circ)))
+        self.n_params, self.n_qubits, self.structure = npar, 2 * n_sites, structure
+        return self
+
+    def setup_problem(self, prob):
+        """Set up from a ``workloads.Problem``."""
+        return self.setup(prob.L, prob.pairs, prob.param_of, prob.n_params, prob.structure,
+                          prob.J, prob.U, prob.t, prob.periodic)
+
+    def set_columns(self, begin: int, end: int):
+        self._check(self._lib.rq_set_columns(self._h, int(begin), int(end)))
+
+    def set_tile(self, columns_per_tile: int = 0, max_dirs: int = 0):
+        self._check(self._lib.rq_set_tile(self._h, int(columns_per_tile), int(max_dirs)))
+
+    def info(self) -> dict:
+        i = RQInfo()
+        self._check(self._lib.rq_get_info(self._h, C.byref(i)))
+        return {name: getattr(i, name) for name, _ in RQInfo._fields_}
+
+    # --- evaluations (host memory) ---------------------------------------
+    def cost(self, gates) -> float:
+        g = _c128(gates)
+        f = C.c_double()
+        self._check(self._lib.rq_cost(self._h, _dptr(g.view(np.float64)), C.byref(f)))
+        return f.value
+
+    def grad(self, gates) -> Tuple[float, np.ndarray]:
+        g = _c128(gates)
+        out = np.empty_like(g)
+        f = C.c_double()
+        self._check(self._lib.rq_grad(self._h, _dptr(g.view(np.float64)), C.byref(f),
+                                      _dptr(out.view(np.float64))))
+        return f.value, out
+
+    def hvp(self, gates, dirs) -> Tuple[float, np.ndarray, np.ndarray]:
+        g = _c128(gates)
+        d = _c128(dirs).reshape((-1,) + g.shape)
+        rg = np.empty_like(g)
+        hv = np.empty_like(d)
+        f = C.c_double()
+        self._check(self._lib.rq_hvp(self._h, _dptr(g.view(np.float64)), _dptr(d.view(np.float64)),
+                                     d.shape[0], C.byref(f), _dptr(rg.view(np.float64)),
+                                     _dptr(hv.view(np.float64))))
+        return f.value, rg, hv
+
+    # --- evaluations (device pointers, stream ordered) ---------------------
+    def cost_dev(self, gates_ptr: int, f_ptr: int):
+        self._check(self._lib.rq_cost_dev(self._h, C.c_void_p(gates_ptr), C.c_void_p(f_ptr)))
+
+    def grad_dev(self, gates_ptr: int, f_ptr: int, rgrad_ptr: int):
+        self._check(self._lib.rq_grad_dev(self._h, C.c_void_p(gates_ptr), C.c_void_p(f_ptr),
+                                          C.c_void_p(rgrad_ptr)))
+
+    def hvp_dev(self, gates_ptr: int, dirs_ptr: int, k: int, f_ptr: int, rgrad_ptr: int, hvps_ptr: int):
+        self._check(self._lib.rq_hvp_dev(self._h, C.c_void_p(gates_ptr), C.c_void_p(dirs_ptr), int(k),
+                                         C.c_void_p(f_ptr), C.c_void_p(rgrad_ptr), C.c_void_p(hvps_ptr)))
+
+    # --- trust region ---------------------------------------------------
+    def tr_step(self, gates: np.ndarray, state: RQTRState) -> np.ndarray:
+        """One trust-region iteration; returns the (possibly updated) gates."""
+        g = _c128(gates).copy()
+        self._check(self._lib.rq_tr_step(self._h, _dptr(g.view(np.float64)), C.byref(state)))
+        return g
+
+    def target_column(self, j: int) -> np.ndarray:
+        out = np.empty(1 << self.n_qubits, dtype=np.complex128)
+        self._check(self._lib.rq_target_column(self._h, int(j), _dptr(out.view(np.float64))))
+        return out
+
+
+def tr_state(radius=0.01, max_radius=0.1, rho_accept=0.125, kappa=0.1, theta=1.0, max_inner=0) -> RQTRState:
+    s = RQTRState()
+    s.radius, s.max_radius, s.rho_accept = radius, max_radius, rho_accept
+    s.kappa, s.theta, s.max_inner = kappa, theta, max_inner
+    return s

@@ -1,0 +1,36 @@
+"""Shared test helpers: tolerance rule and cached oracle targets."""
+import functools
+
+import numpy as np
+
+RTOL = 1e-12  # relative tolerance of every FP64 parity comparison
+
+
+def floor(n: int) -> float:
+    """Absolute floor s = 1e-6 * 2^n of the relative test (results near an
+    optimum are small; a pure relative test would be meaningless there)."""
+    return 1e-6 * 2.0 ** n
+
+
+def assert_close(got, ref, n: int, rtol: float = RTOL, what: str = ""):
+    """Norm-wise ``||got - ref|| <= rtol * max(||ref||, s)`` over all entries."""
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    err = float(np.linalg.norm(np.ravel(got - ref)))
+    scale = max(float(np.linalg.norm(np.ravel(ref))), floor(n))
+    assert err <= rtol * scale, f"{what}: |err| = {err:.3e} > {rtol:.0e} * {scale:.3e} (rel {err / scale:.2e})"
+
+
+@functools.lru_cache(maxsize=None)
+def sector_target(L, J, U, t, periodic):
+    from oracle import model
+    return model.SectorTarget(L, J, U, t, periodic)
+
+
+def target_for(prob):
+    return sector_target(prob.L, prob.J, prob.U, prob.t, prob.periodic)
+
+
+def oracle_eval(prob, cols, Xraw=None, gates=None, chunk=16):
+    from oracle import statevector as sv
+    return sv.cost_grad_hvp(prob, target_for(prob), list(cols), Xraw, gates=gates, chunk=chunk)
