@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark: cost + Riemannian gradient + one Riemannian HVP, n = 16, FP64.
+
+Workload: spinful Fermi-Hubbard chain of 8 sites (n = 16 qubits, open, J = 1,
+U = 4, t = 0.5), brickwall of 11 layers ``ABCBABCBABC`` = 78 general U(4)
+gates (Trotter start + seeded noise, seed 1601), one raw HVP direction
+(seed 1602).  One evaluation ("eval") is f, grad f and Hess f[X] summed over
+all 2^16 basis columns.  A step is one pass of the whole path over one batch
+of basis columns (one column tile); ``value`` = evals/s = columns processed /
+2^16 / time.  Batches rotate through the basis; every tile is far larger than
+the 129 MB L2 (512 columns x 1 MiB per state).
+
+``--impl reference`` times the CPU oracle (the paper's matrix-free algorithm
+in numpy) on the host cores on a bounded column sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "f+grad+HVP evals/sec at n=16 FP64 (% HBM roofline); batched/served vs plain"
+UNIT = "evals/s"
+N_QUBITS = 16
+N_COLS = 1 << N_QUBITS
+# FP64 peak of the GB300 ALU path: 2 DFMA (4 flops) per clock per SM x 152 SMs
+# x 2.07 GHz maximum SM clock (a DFMA probe on this part measured 1.19 TFLOP/s
+# at 1.99 GHz, i.e. the same 4 flops/clock/SM).
+FP64_PEAK_TFLOPS = 4 * 152 * 2.07e9 / 1e12
+HBM_FALLBACK_GBS = 6800.0
+
+WORKLOAD = ("spinful Fermi-Hubbard chain, 8 sites (n=16 qubits), open, J=1 U=4 t=0.5; "
+            "brickwall 11 layers ABCBABCBABC, 78 U(4) gates (Trotter + noise, seed 1601); "
+            "f + Riemannian grad + 1 Riemannian HVP (direction seed 1602) summed over all 65536 basis columns")
+
+
+def _measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons sampled during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        if not getattr(self, "lines", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------- CPU baseline ----
+
+def _oracle_worker(args):
+    """Time the CPU oracle on a few columns (runs in a spawned process)."""
+    cols, structure, threads = args
+    os.environ.setdefault("OMP_NUM_THREADS", str(threads))
+    sys.path.insert(0, ROOT)
+    import workloads as w
+    from oracle import model, statevector as sv
+    prob = w.config_problem("n16", structure=structure)
+    X = w.random_directions(prob.n_params, 1, 1602)
+    st = model.SectorTarget(prob.L, prob.J, prob.U, prob.t, prob.periodic)
+    for j in cols:                      # target blocks are set-up, not timed
+        st.column(int(j))
+    t0 = time.perf_counter()
+    sv.cost_grad_hvp(prob, st, list(cols), X, chunk=len(cols))
+    return time.perf_counter() - t0
+
+
+def _sample_columns(count: int):
+    # columns of the (4 up, 4 down) sector, the most common sector size
+    out = []
+    for x in range(N_COLS):
+        if bin(x >> 8).count("1") == 4 and bin(x & 255).count("1") == 4:
+            out.append(x)
+            if len(out) == count:
+                break
+    return out
+
+
+def cpu_oracle_rate(per_worker: int = 1, workers: int = 0, structure: int = 0, repeats: int = 1):
+    """Oracle evals/s on ``workers`` host processes, each timing ``per_worker`` columns."""
+    import multiprocessing as mp
+    workers = workers or os.cpu_count() or 1
+    cols = _sample_columns(workers * per_worker * repeats)
+    ctx = mp.get_context("spawn")
+    rates = []
+    with ctx.Pool(workers) as pool:
+        for r in range(repeats):
+            chunk = cols[r * workers * per_worker:(r + 1) * workers * per_worker]
+            jobs = [(chunk[i * per_worker:(i + 1) * per_worker], structure, 1) for i in range(workers)]
+            times = pool.map(_oracle_worker, jobs)
+            rates.append((workers * per_worker / N_COLS) / max(times))
+    return rates, workers, len(cols)
+
+
+# ----------------------------------------------------------------- our arm --
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+
+    from paper_2506_23775_gb300 import _build
+    if rank == 0 or local == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    import workloads as w
+    from paper_2506_23775_gb300 import rq
+
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", local)
+
+    def measure(structure: int, steps: int, warmup: int, tile: int):
+        prob = w.config_problem("n16", structure=structure)
+        X = w.random_directions(prob.n_params, 1, 1602)
+        ctx = rq.Context(local, stream=stream.cuda_stream).setup_problem(prob)
+        if tile:
+            ctx.set_tile(tile, 1)
+        ctx.set_columns(0, min(N_COLS, 512 if not tile else tile))
+        B = ctx.info()["columns_per_tile"]
+        batch = B if structure == 0 else 2 * B      # parity: one even + one odd tile per batch
+        gates = torch.from_numpy(prob.gates.copy()).to(dev)
+        dirs = torch.from_numpy(X.copy()).to(dev)
+        f_t = torch.zeros(1, dtype=torch.float64, device=dev)
+        rg_t = torch.zeros_like(gates)
+        hv_t = torch.zeros_like(dirs)
+
+        def batch_range(s):
+            c0 = ((rank * (steps + warmup) + s) * batch) % N_COLS
+            return c0, c0 + batch
+
+        def step(s):
+            ctx.set_columns(*batch_range(s))
+            ctx.hvp_dev(gates.data_ptr(), dirs.data_ptr(), 1, f_t.data_ptr(), rg_t.data_ptr(), hv_t.data_ptr())
+
+        for s in range(warmup):
+            step(s)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        launches0 = ctx.info()["kernel_launches"]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            ctx.profile_start()
+            e0.record(stream)
+            for s in range(warmup, warmup + steps):
+                step(s)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            prof = ctx.profile_stop()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = ctx.info()["kernel_launches"] - launches0
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        value = world * steps * batch / N_COLS / (ms_max * 1e-3)
+
+        # end to end through the host C-ABI call: pinned host inputs/outputs
+        g_h = torch.from_numpy(prob.gates.copy()).pin_memory().numpy()
+        d_h = torch.from_numpy(X.copy()).pin_memory().numpy()
+        rg_h = torch.empty(g_h.shape, dtype=torch.complex128).pin_memory().numpy()
+        hv_h = torch.empty(d_h.shape, dtype=torch.complex128).pin_memory().numpy()
+        e2e_steps = max(2, steps // 2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(e2e_steps):
+            ctx.set_columns(*batch_range(s))
+            ctx.hvp(g_h, d_h, out=(rg_h, hv_h))
+        e2e_s = time.perf_counter() - t0
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * e2e_steps * batch / N_COLS / float(tt.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(g_h.nbytes + d_h.nbytes),
+               "d2h_bytes_per_step": int(8 + rg_h.nbytes + hv_h.nbytes)}
+        info = ctx.info()
+        ctx.close()
+        return dict(value=value, ms_per_step=ms_max / steps, launches=launches, prof=prof, clocks=clk.summary(),
+                    e2e=e2e, batch=batch, B=B, info=info)
+
+    gen = measure(0, args.steps, args.warmup, args.tile)
+    par = None
+    if not args.general_only:
+        par = measure(1, args.steps, args.warmup, args.tile)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    hbm, hbm_src = _measured_hbm()
+
+    def roofline(res):
+        sweep = {k: v for k, v in res["prof"].items() if k.startswith(("fwd", "bwd"))}
+        dom = max(sweep, key=lambda k: sweep[k]["ms"])
+        d = sweep[dom]
+        per_launch_ms = d["ms"] / d["launches"]
+        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+        fam = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                   "share": round(v["ms"] / sum(x["ms"] for x in res["prof"].values()), 4),
+                   "tflops": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 4),
+                   "gbs": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)} for k, v in res["prof"].items()}
+        return {"kernel": dom, "bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (FP64)",
+                "flops_per_launch": d["flops"] / d["launches"], "launch_ms": round(per_launch_ms, 4),
+                "hbm_achieved_gbs": round(d["bytes"] / (d["ms"] * 1e-3) / 1e9, 1),
+                "hbm_frac": round(d["bytes"] / (d["ms"] * 1e-3) / 1e9 / hbm, 4),
+                "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src, "families": fam}
+
+    line = {
+        "metric": METRIC, "value": gen["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": gen["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "structure": "general", "columns_per_step": gen["batch"],
+                   "columns_per_tile": gen["B"], "hvp_directions": 1,
+                   "l2": "inputs larger than L2 (each tile state is 512 MiB)",
+                   "parallelism": f"column shards x{world}" if world > 1 else "single GPU"},
+        "roofline": roofline(gen), "e2e": gen["e2e"], "gpu_launches": gen["launches"], "clocks": gen["clocks"],
+    }
+    if par is not None:
+        line["parity"] = {"value": par["value"], "unit": UNIT, "ms_per_step": par["ms_per_step"],
+                          "columns_per_step": par["batch"], "e2e": par["e2e"], "roofline": roofline(par),
+                          "gpu_launches": par["launches"], "clocks": par["clocks"],
+                          "structure": "parity-conserving gates, parity-sector tiles (2^15 stored amplitudes)"}
+    if world == 1 and not args.no_cpu:
+        rates, cores, ncols = cpu_oracle_rate(per_worker=1)
+        line["cpu_baseline"] = {"value": rates[0], "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{cores} basis columns of the (4,4) sector, one per spawned process, "
+                                          "numpy oracle (paper's matrix-free algorithm), general gates; "
+                                          "evals/s = columns / 65536 / slowest process time"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------ reference arm --
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    # warm-up and timed steps: each step times `cores` columns, one per process
+    rates, cores, ncols = cpu_oracle_rate(per_worker=1, workers=cores, repeats=args.warmup + args.steps)
+    timed = rates[args.warmup:]
+    value = len(timed) / sum(1.0 / r for r in timed)  # columns per second over all timed steps
+    ms_per_step = 1e3 * (cores / N_COLS) / value
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "structure": "general", "columns_per_step": cores},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: {cores} basis columns of the (4,4) sector, one per spawned "
+                                   "process (numpy oracle, the paper's matrix-free algorithm)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--tile", type=int, default=0, help="columns per tile (power of two; 0 = automatic)")
+    ap.add_argument("--general-only", action="store_true", help="skip the parity-gate measurement")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

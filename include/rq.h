@@ -188,6 +188,25 @@ rq_status rq_target_column(rq_ctx *ctx, int64_t j, double *out);
 /* Sizes and counters of the context. */
 rq_status rq_get_info(const rq_ctx *ctx, rq_info_t *info);
 
+/* Per-kernel timing of one context (benchmarking and roofline accounting).
+ * Between rq_profile_start and rq_profile_stop every kernel the context
+ * launches is bracketed by CUDA events on the context stream.  One record per
+ * kernel family: launches, summed device time (ms) and the algorithmic FP64
+ * flops (8 per complex multiply-add) and DRAM bytes (each input read once,
+ * each output written once) of those launches.  `name` points to a static
+ * string.  rq_profile_stop synchronises the stream, writes at most
+ * `capacity` records and sets *n_stats to the number of families seen. */
+typedef struct {
+    const char *name;
+    int64_t launches;
+    double total_ms;
+    double flops;
+    double bytes;
+} rq_kernel_stat;
+
+rq_status rq_profile_start(rq_ctx *ctx);
+rq_status rq_profile_stop(rq_ctx *ctx, rq_kernel_stat *stats, int capacity, int *n_stats);
+
 /* Text of the last error on this context ("" if none); valid until the next
  * call on the context.  NULL ctx: the last rq_create failure. */
 const char *rq_last_error(const rq_ctx *ctx);

@@ -69,11 +69,47 @@ struct rq_ctx {
     long long out_cap = 0;
     long long problem_bytes = 0, work_bytes = 0, small_bytes = 0;
     long long launches = 0;
+    long long cols_cap = 0;
+    // per-kernel profiling (events bracket every launch while enabled)
+    struct ProfRec {
+        int family;
+        cudaEvent_t a, b;
+        double flops, bytes;
+    };
+    bool prof_on = false;
+    std::vector<ProfRec> prof;
+    size_t prof_used = 0;
 };
 
 namespace {
 
 std::string g_create_error;
+
+enum Family : int { kFamFwd = 0, kFamBwdDir, kFamBwdBase, kFamTarget, kFamInit, kFamReduce, kFamGeometry, kFamCheb, kFamCount };
+const char *const kFamilyName[kFamCount] = {"fwd_gate", "bwd_gate_dir", "bwd_gate_base", "target_scatter_cost",
+                                            "init_unit", "reduce", "geometry", "target_chebyshev"};
+
+// Event bracket of one launch while profiling is on.
+struct ProfScope {
+    rq_ctx *ctx;
+    rq_ctx::ProfRec *rec = nullptr;
+    ProfScope(rq_ctx *c, int family, double flops, double bytes) : ctx(c) {
+        if (!ctx->prof_on) return;
+        if (ctx->prof_used == ctx->prof.size()) {
+            rq_ctx::ProfRec r{};
+            if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return;
+            ctx->prof.push_back(r);
+        }
+        rec = &ctx->prof[ctx->prof_used++];
+        rec->family = family;
+        rec->flops = flops;
+        rec->bytes = bytes;
+        cudaEventRecord(rec->a, ctx->stream);
+    }
+    ~ProfScope() {
+        if (rec) cudaEventRecord(rec->b, ctx->stream);
+    }
+};
 
 rq_status fail(rq_ctx *ctx, rq_status code, const char *fmt, ...) {
     char buf[512];
@@ -133,7 +169,6 @@ void free_workspace(rq_ctx *ctx) {
     dev_free(ctx->d_part);
     dev_free(ctx->d_partd);
     dev_free(ctx->d_fpart);
-    dev_free(ctx->d_cols);
     ctx->work_bytes = 0;
 }
 
@@ -147,6 +182,8 @@ void free_small(rq_ctx *ctx) {
     dev_free(ctx->d_dirs_raw);
     dev_free(ctx->d_param_of);
     dev_free(ctx->d_out);
+    dev_free(ctx->d_cols);
+    ctx->cols_cap = 0;
     ctx->envd_cap = ctx->dirs_cap = 0;
     ctx->out_cap = 0;
     ctx->small_bytes = 0;
@@ -198,10 +235,10 @@ long long bytes_per_column(const rq_ctx *ctx, int kc) {
 }
 
 // Choose B (columns per tile) and kc (directions per sweep), build the tile
-// column table and allocate the sweep workspace.
+// column table and (re)allocate the sweep workspace.  A new column range with
+// the same B and kc only re-uploads the column table.
 rq_status rebuild_tiles(rq_ctx *ctx) {
     RQ_CUDA(cudaStreamSynchronize(ctx->stream));
-    free_workspace(ctx);
     std::vector<std::vector<int32_t>> groups;
     std::vector<int> gpar;
     column_groups(ctx, groups, gpar);
@@ -210,7 +247,8 @@ rq_status rebuild_tiles(rq_ctx *ctx) {
     const int bcap = ctx->user_B > 0 ? ctx->user_B : (int)std::min<long long>(512, 1LL << ilog2(largest));
     size_t free_b = 0, total_b = 0;
     RQ_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    const double budget = std::min(0.6 * (double)free_b, 96.0 * (1LL << 30));
+    const double avail = (double)free_b + (double)ctx->work_bytes;  // the current workspace can be reused
+    const double budget = std::min(0.6 * avail, 96.0 * (1LL << 30));
     int B = 0, kc = 1;
     const int kc_opts[2] = {rq::kMaxDirs, 1};
     const int n_opts = ctx->user_kc > 0 ? 1 : 2;
@@ -227,32 +265,44 @@ rq_status rebuild_tiles(rq_ctx *ctx) {
     if (B == 0)
         return fail(ctx, RQ_ENOMEM, "one column needs %lld bytes of workspace, %.0f available",
                     bytes_per_column(ctx, 1), budget);
-    ctx->B = B;
-    ctx->log2B = ilog2(B);
-    ctx->kc = kc;
+    const long long items = std::max<long long>(1, ctx->n_store / 4 * B);
+    const int ncta = (int)std::min<long long>((long long)ctx->sms * rq::kCtasPerSm, (items + rq::kThreads - 1) / rq::kThreads);
     std::vector<int32_t> cols;
-    ctx->tile_parity.clear();
+    std::vector<int> tpar;
     for (size_t gi = 0; gi < groups.size(); ++gi) {
         const auto &gr = groups[gi];
         for (size_t s = 0; s < gr.size(); s += B) {
             for (int b = 0; b < B; ++b) cols.push_back(s + b < gr.size() ? gr[s + b] : -1);
-            ctx->tile_parity.push_back(gpar[gi]);
+            tpar.push_back(gpar[gi]);
         }
     }
-    ctx->n_tiles = (int)ctx->tile_parity.size();
-    const long long tile = ctx->n_store * B;
-    const long long items = std::max<long long>(1, ctx->n_store / 4 * B);
-    ctx->ncta = (int)std::min<long long>((long long)ctx->sms * rq::kCtasPerSm, (items + rq::kThreads - 1) / rq::kThreads);
-    RQ_TRY(dev_alloc(ctx, &ctx->d_psi, tile * (ctx->g + 1), ctx->work_bytes));
-    RQ_TRY(dev_alloc(ctx, &ctx->d_dpsi, tile * (ctx->g + 1) * kc, ctx->work_bytes));
-    RQ_TRY(dev_alloc(ctx, &ctx->d_lam, tile, ctx->work_bytes));
-    RQ_TRY(dev_alloc(ctx, &ctx->d_dlam, tile * kc, ctx->work_bytes));
-    RQ_TRY(dev_alloc(ctx, &ctx->d_part, (long long)ctx->g * ctx->ncta * rq::kEnvDoubles, ctx->work_bytes));
-    RQ_TRY(dev_alloc(ctx, &ctx->d_partd, (long long)kc * ctx->g * ctx->ncta * rq::kEnvDoubles, ctx->work_bytes));
-    RQ_TRY(dev_alloc(ctx, &ctx->d_fpart, B, ctx->work_bytes));
+    const bool same = ctx->d_psi && B == ctx->B && kc == ctx->kc && ncta == ctx->ncta;
+    if (!same) {
+        free_workspace(ctx);
+        ctx->B = B;
+        ctx->log2B = ilog2(B);
+        ctx->kc = kc;
+        ctx->ncta = ncta;
+        const long long tile = ctx->n_store * B;
+        RQ_TRY(dev_alloc(ctx, &ctx->d_psi, tile * (ctx->g + 1), ctx->work_bytes));
+        RQ_TRY(dev_alloc(ctx, &ctx->d_dpsi, tile * (ctx->g + 1) * kc, ctx->work_bytes));
+        RQ_TRY(dev_alloc(ctx, &ctx->d_lam, tile, ctx->work_bytes));
+        RQ_TRY(dev_alloc(ctx, &ctx->d_dlam, tile * kc, ctx->work_bytes));
+        RQ_TRY(dev_alloc(ctx, &ctx->d_part, (long long)ctx->g * ncta * rq::kEnvDoubles, ctx->work_bytes));
+        RQ_TRY(dev_alloc(ctx, &ctx->d_partd, (long long)kc * ctx->g * ncta * rq::kEnvDoubles, ctx->work_bytes));
+        RQ_TRY(dev_alloc(ctx, &ctx->d_fpart, B, ctx->work_bytes));
+    }
+    if ((long long)cols.size() > ctx->cols_cap) {
+        dev_free(ctx->d_cols);
+        ctx->cols_cap = 0;
+        RQ_TRY(dev_alloc(ctx, &ctx->d_cols, (long long)cols.size(), ctx->small_bytes));
+        ctx->cols_cap = (long long)cols.size();
+    }
+    ctx->tile_parity = tpar;
+    ctx->n_tiles = (int)tpar.size();
     if (!cols.empty()) {
-        RQ_TRY(dev_alloc(ctx, &ctx->d_cols, (long long)cols.size(), ctx->work_bytes));
-        RQ_CUDA(cudaMemcpyAsync(ctx->d_cols, cols.data(), cols.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+        RQ_CUDA(cudaMemcpyAsync(ctx->d_cols, cols.data(), cols.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                ctx->stream));
         RQ_CUDA(cudaStreamSynchronize(ctx->stream));
     }
     return RQ_OK;
@@ -272,7 +322,8 @@ rq_status ensure_small(rq_ctx *ctx, int k) {
         RQ_TRY(dev_alloc(ctx, &ctx->d_envd, (long long)cap * ctx->g * rq::kEnvDoubles, ctx->small_bytes));
         ctx->dirs_cap = ctx->envd_cap = cap;
     }
-    const long long need = 1 + (long long)(1 + ctx->dirs_cap) * ctx->P * 32;
+    // f at [0], then 16-byte aligned complex outputs from [2]
+    const long long need = 2 + (long long)(1 + ctx->dirs_cap) * ctx->P * 32;
     if (need > ctx->out_cap) {
         dev_free(ctx->d_out);
         RQ_TRY(dev_alloc(ctx, &ctx->d_out, need, ctx->small_bytes));
@@ -386,7 +437,10 @@ rq_status build_target(rq_ctx *ctx) {
         if (!bonds.empty())
             cudaMemcpyAsync(d_bonds, bonds.data(), bonds.size() * sizeof(long long), cudaMemcpyHostToDevice, ctx->stream);
         const rq::TargetDev td = target_dev(ctx);
-        rq::launch_cheb_init(ctx->d_off_u, d_sizes, ctx->S, ctx->u_entries, tA, ctx->d_U, coef(0), ctx->stream);
+        {
+            ProfScope ps(ctx, kFamCheb, 0.0, 0.0);
+            rq::launch_cheb_init(ctx->d_off_u, d_sizes, ctx->S, ctx->u_entries, tA, ctx->d_U, coef(0), ctx->stream);
+        }
         ++ctx->launches;
         const double dscale = alpha > 0 ? 1.0 / alpha : 0.0, hop = alpha > 0 ? -J / alpha : 0.0;
         double *prev = tA, *cur = tB;
@@ -419,12 +473,20 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
     if (k < 0) return fail(ctx, RQ_EINVAL, "k = %d < 0", k);
     if (!gates) return fail(ctx, RQ_EINVAL, "gates is NULL");
     if (k > 0 && !dirs) return fail(ctx, RQ_EINVAL, "dirs is NULL with k = %d", k);
+    // complex128 arrays are read and written as 16-byte double2
+    const auto misaligned = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) != 0; };
+    if (misaligned(gates) || (k > 0 && misaligned(dirs)) || (rgrad && misaligned(rgrad)) || (hvps && misaligned(hvps)))
+        return fail(ctx, RQ_EINVAL, "gates, dirs, rgrad and hvps must be 16-byte aligned device pointers");
     RQ_TRY(ensure_small(ctx, k));
     cudaStream_t s = ctx->stream;
     const int g = ctx->g, P = ctx->P;
-    rq::launch_mask_gates(reinterpret_cast<const double2 *>(gates), ctx->d_gates, P, ctx->structure, s);
+    {
+        ProfScope ps(ctx, kFamGeometry, 0.0, 2.0 * P * 16 * sizeof(double2));
+        rq::launch_mask_gates(reinterpret_cast<const double2 *>(gates), ctx->d_gates, P, ctx->structure, s);
+    }
     RQ_LAUNCHED();
     if (k > 0) {
+        ProfScope ps(ctx, kFamGeometry, 0.0, 2.0 * k * P * 16 * sizeof(double2));
         rq::launch_project_dirs(ctx->d_gates, reinterpret_cast<const double2 *>(dirs), ctx->d_dirs, P, k,
                                 ctx->structure, s);
         RQ_LAUNCHED();
@@ -446,7 +508,10 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
             const int32_t *cols = ctx->d_cols + (long long)ti * B;
             const int par = ctx->tile_parity[ti];
             RQ_CUDA(cudaMemsetAsync(ctx->d_psi, 0, sizeof(double2) * tile, s));
-            rq::launch_init_unit(ctx->d_psi, cols, B, ctx->log2B, ctx->n_store, ctx->structure, s);
+            {
+                ProfScope ps(ctx, kFamInit, 0.0, (double)B * sizeof(double2));
+                rq::launch_init_unit(ctx->d_psi, cols, B, ctx->log2B, ctx->n_store, ctx->structure, s);
+            }
             RQ_LAUNCHED();
             for (int d = 0; d < kd; ++d) RQ_CUDA(cudaMemsetAsync(ctx->d_dpsi + d * set, 0, sizeof(double2) * tile, s));
             // forward pass
@@ -466,16 +531,28 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                 a.log2B = ctx->log2B;
                 a.tile_parity = par;
                 a.n_items = (geo.mode == rq::kParity2 ? ctx->n_store / 2 : ctx->n_store / 4) * B;
-                rq::launch_fwd(a, ctx->ncta, s);
+                {
+                    const double amps = geo.mode == rq::kParity2 ? 2.0 : 4.0;
+                    const double cm = geo.mode == rq::kGeneral ? 16.0 : (geo.mode == rq::kParity4 ? 8.0 : 4.0);
+                    ProfScope ps(ctx, kFamFwd, (double)a.n_items * 8.0 * cm * (1 + 2 * kd),
+                                 (double)a.n_items * amps * sizeof(double2) * 2 * (1 + kd));
+                    rq::launch_fwd(a, ctx->ncta, s);
+                }
                 RQ_LAUNCHED();
             }
             // adjoint start lambda_g = U|j> and the cost summands
             RQ_CUDA(cudaMemsetAsync(ctx->d_lam, 0, sizeof(double2) * tile, s));
-            rq::launch_scatter_target(target_dev(ctx), cols, B, ctx->log2B, ctx->structure, ctx->n, ctx->d_lam,
-                                      ctx->d_psi + g * tile, ctx->d_fpart, s);
+            {
+                ProfScope ps(ctx, kFamTarget, 0.0, 0.0);
+                rq::launch_scatter_target(target_dev(ctx), cols, B, ctx->log2B, ctx->structure, ctx->n, ctx->d_lam,
+                                          ctx->d_psi + g * tile, ctx->d_fpart, s);
+            }
             RQ_LAUNCHED();
             if (first) {
-                rq::launch_reduce_f(ctx->d_fpart, B, ctx->d_facc, s);
+                {
+                    ProfScope ps(ctx, kFamReduce, 0.0, (double)B * sizeof(double));
+                    rq::launch_reduce_f(ctx->d_fpart, B, ctx->d_facc, s);
+                }
                 RQ_LAUNCHED();
             }
             if (!backward) continue;
@@ -499,7 +576,13 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                     b.dir = ctx->d_dirs + ((long long)(d0 + d) * P + geo.param) * 16;
                     b.accumulate = 1;
                     b.part = ctx->d_partd + ((long long)d * g + l) * ctx->ncta * rq::kEnvDoubles;
-                    rq::launch_bwd_dir(b, ctx->ncta, s);
+                    {
+                        const double amps = geo.mode == rq::kParity2 ? 2.0 : 4.0;
+                        const double cm = geo.mode == rq::kGeneral ? 16.0 : (geo.mode == rq::kParity4 ? 8.0 : 4.0);
+                        ProfScope ps(ctx, kFamBwdDir, (double)b.n_items * 8.0 * cm * (2 + 2 * b.update),
+                                     (double)b.n_items * amps * sizeof(double2) * (4 + b.update));
+                        rq::launch_bwd_dir(b, ctx->ncta, s);
+                    }
                     RQ_LAUNCHED();
                 }
                 if (l > 0 || acc_env) {
@@ -508,24 +591,40 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                     a.dir = nullptr;
                     a.accumulate = acc_env ? 1 : 0;
                     a.part = ctx->d_part + (long long)l * ctx->ncta * rq::kEnvDoubles;
-                    rq::launch_bwd_base(a, ctx->ncta, s);
+                    {
+                        const double amps = geo.mode == rq::kParity2 ? 2.0 : 4.0;
+                        const double cm = geo.mode == rq::kGeneral ? 16.0 : (geo.mode == rq::kParity4 ? 8.0 : 4.0);
+                        ProfScope ps(ctx, kFamBwdBase, (double)a.n_items * 8.0 * cm * (a.accumulate + a.update),
+                                     (double)a.n_items * amps * sizeof(double2) * (1 + a.accumulate + a.update));
+                        rq::launch_bwd_base(a, ctx->ncta, s);
+                    }
                     RQ_LAUNCHED();
                 }
             }
             if (acc_env) {
-                rq::launch_reduce_env(ctx->d_part, ctx->ncta, g, ctx->d_env, s);
+                {
+                    ProfScope ps(ctx, kFamReduce, 0.0, (double)g * ctx->ncta * rq::kEnvDoubles * sizeof(double));
+                    rq::launch_reduce_env(ctx->d_part, ctx->ncta, g, ctx->d_env, s);
+                }
                 RQ_LAUNCHED();
             }
             for (int d = 0; d < kd; ++d) {
-                rq::launch_reduce_env(ctx->d_partd + (long long)d * g * ctx->ncta * rq::kEnvDoubles, ctx->ncta, g,
-                                      ctx->d_envd + (long long)(d0 + d) * g * rq::kEnvDoubles, s);
+                {
+                    ProfScope ps(ctx, kFamReduce, 0.0, (double)g * ctx->ncta * rq::kEnvDoubles * sizeof(double));
+                    rq::launch_reduce_env(ctx->d_partd + (long long)d * g * ctx->ncta * rq::kEnvDoubles, ctx->ncta, g,
+                                          ctx->d_envd + (long long)(d0 + d) * g * rq::kEnvDoubles, s);
+                }
                 RQ_LAUNCHED();
             }
         }
     }
-    rq::launch_geometry(ctx->d_gates, ctx->d_dirs, ctx->d_env, ctx->d_envd, ctx->d_param_of, g, P, k,
-                        ctx->structure, ctx->d_facc, f_out, want_env ? reinterpret_cast<double2 *>(rgrad) : nullptr,
-                        reinterpret_cast<double2 *>(hvps), s);
+    {
+        ProfScope ps(ctx, kFamGeometry, 0.0, 0.0);
+        rq::launch_geometry(ctx->d_gates, ctx->d_dirs, ctx->d_env, ctx->d_envd, ctx->d_param_of, g, P, k,
+                            ctx->structure, ctx->d_facc, f_out,
+                            want_env ? reinterpret_cast<double2 *>(rgrad) : nullptr,
+                            reinterpret_cast<double2 *>(hvps), s);
+    }
     RQ_LAUNCHED();
     return RQ_OK;
 }
@@ -549,7 +648,7 @@ rq_status eval_host(rq_ctx *ctx, const double *gates, const double *dirs, int k,
     const long long gsz = (long long)ctx->P * 32;
     RQ_CUDA(cudaMemcpyAsync(ctx->d_in_gates, gates, sizeof(double) * gsz, cudaMemcpyHostToDevice, s));
     if (k > 0) RQ_CUDA(cudaMemcpyAsync(ctx->d_dirs_raw, dirs, sizeof(double) * gsz * k, cudaMemcpyHostToDevice, s));
-    double *o_f = ctx->d_out, *o_g = ctx->d_out + 1, *o_h = ctx->d_out + 1 + gsz;
+    double *o_f = ctx->d_out, *o_g = ctx->d_out + 2, *o_h = ctx->d_out + 2 + gsz;
     RQ_TRY(eval_dev(ctx, reinterpret_cast<const double *>(ctx->d_in_gates),
                     reinterpret_cast<const double *>(ctx->d_dirs_raw), k, want_env != 0, o_f, o_g, o_h));
     if (f) RQ_CUDA(cudaMemcpyAsync(f, o_f, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -597,6 +696,10 @@ rq_status rq_destroy(rq_ctx *ctx) {
     if (!ctx) return RQ_OK;
     cudaSetDevice(ctx->device);
     free_problem(ctx);
+    for (auto &r : ctx->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return RQ_OK;
@@ -766,6 +869,39 @@ rq_status rq_get_info(const rq_ctx *ctx, rq_info_t *info) {
     info->max_dirs = ctx->kc;
     info->workspace_bytes = ctx->problem_bytes + ctx->work_bytes + ctx->small_bytes;
     info->target_entries = ctx->u_entries;
+    return RQ_OK;
+}
+
+rq_status rq_profile_start(rq_ctx *ctx) {
+    if (!ctx) return RQ_EINVAL;
+    ctx->prof_on = true;
+    ctx->prof_used = 0;
+    return RQ_OK;
+}
+
+rq_status rq_profile_stop(rq_ctx *ctx, rq_kernel_stat *stats, int capacity, int *n_stats) {
+    if (!ctx) return RQ_EINVAL;
+    ctx->prof_on = false;
+    RQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    rq_kernel_stat acc[kFamCount];
+    for (int i = 0; i < kFamCount; ++i) acc[i] = rq_kernel_stat{kFamilyName[i], 0, 0.0, 0.0, 0.0};
+    for (size_t i = 0; i < ctx->prof_used; ++i) {
+        const auto &r = ctx->prof[i];
+        float ms = 0.0f;
+        RQ_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+        acc[r.family].launches += 1;
+        acc[r.family].total_ms += ms;
+        acc[r.family].flops += r.flops;
+        acc[r.family].bytes += r.bytes;
+    }
+    ctx->prof_used = 0;
+    int n = 0;
+    for (int i = 0; i < kFamCount; ++i) {
+        if (acc[i].launches == 0) continue;
+        if (stats && n < capacity) stats[n] = acc[i];
+        ++n;
+    }
+    if (n_stats) *n_stats = n;
     return RQ_OK;
 }
 

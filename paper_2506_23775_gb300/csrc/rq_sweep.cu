@@ -234,13 +234,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_base(const BwdArgs a) {
         if (MODE == kGeneral || MODE == kParity4) {
             long long off[4];
             offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
-            double2 l[4], p[4];
+            double2 l[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                l[c] = a.lam[off[c]];
-                p[c] = __ldg(&a.psi[off[c]]);
-            }
+            for (int c = 0; c < 4; ++c) l[c] = a.lam[off[c]];
             if (accumulate) {
+                double2 p[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) p[c] = __ldg(&a.psi[off[c]]);
                 if (MODE == kGeneral) {
 #pragma unroll
                     for (int i = 0; i < 4; ++i)

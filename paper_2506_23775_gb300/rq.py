@@ -21,7 +21,8 @@ RQ_OK, RQ_EINVAL, RQ_ENOMEM, RQ_ECUDA, RQ_ETIMEOUT, RQ_ESTATE = 0, -1, -2, -3, -
 # Every symbol declared in include/rq.h.
 EXPORTS = ("rq_create", "rq_destroy", "rq_setup_target", "rq_set_columns", "rq_set_tile",
            "rq_cost", "rq_grad", "rq_hvp", "rq_cost_dev", "rq_grad_dev", "rq_hvp_dev",
-           "rq_tr_step", "rq_target_column", "rq_get_info", "rq_last_error")
+           "rq_tr_step", "rq_target_column", "rq_get_info", "rq_profile_start", "rq_profile_stop",
+           "rq_last_error")
 
 
 class RQCircuit(C.Structure):
@@ -49,6 +50,11 @@ class RQInfo(C.Structure):
                 ("columns", C.c_int64), ("columns_per_tile", C.c_int), ("n_tiles", C.c_int),
                 ("max_dirs", C.c_int), ("workspace_bytes", C.c_int64),
                 ("target_entries", C.c_int64), ("kernel_launches", C.c_int64)]
+
+
+class RQKernelStat(C.Structure):
+    _fields_ = [("name", C.c_char_p), ("launches", C.c_int64), ("total_ms", C.c_double),
+                ("flops", C.c_double), ("bytes", C.c_double)]
 
 
 class RQError(RuntimeError):
@@ -82,6 +88,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "rq_tr_step": ([vp, dp, C.POINTER(RQTRState)], C.c_int),
         "rq_target_column": ([vp, i64, dp], C.c_int),
         "rq_get_info": ([vp, C.POINTER(RQInfo)], C.c_int),
+        "rq_profile_start": ([vp], C.c_int),
+        "rq_profile_stop": ([vp, C.POINTER(RQKernelStat), C.c_int, C.POINTER(C.c_int)], C.c_int),
         "rq_last_error": ([vp], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -188,11 +196,19 @@ class Context:
                                       _dptr(out.view(np.float64))))
         return f.value, out
 
-    def hvp(self, gates, dirs) -> Tuple[float, np.ndarray, np.ndarray]:
+    def hvp(self, gates, dirs, out: Optional[Tuple[np.ndarray, np.ndarray]] = None
+            ) -> Tuple[float, np.ndarray, np.ndarray]:
+        """f, Riemannian gradient and HVPs; ``out=(rgrad, hvps)`` reuses
+        caller arrays (for example pinned host memory)."""
         g = _c128(gates)
         d = _c128(dirs).reshape((-1,) + g.shape)
-        rg = np.empty_like(g)
-        hv = np.empty_like(d)
+        if out is None:
+            rg = np.empty_like(g)
+            hv = np.empty_like(d)
+        else:
+            rg, hv = out
+            assert rg.dtype == np.complex128 and rg.shape == g.shape and rg.flags.c_contiguous
+            assert hv.dtype == np.complex128 and hv.shape == d.shape and hv.flags.c_contiguous
         f = C.c_double()
         self._check(self._lib.rq_hvp(self._h, _dptr(g.view(np.float64)), _dptr(d.view(np.float64)),
                                      d.shape[0], C.byref(f), _dptr(rg.view(np.float64)),
@@ -217,6 +233,18 @@ class Context:
         g = _c128(gates).copy()
         self._check(self._lib.rq_tr_step(self._h, _dptr(g.view(np.float64)), C.byref(state)))
         return g
+
+    def profile_start(self):
+        self._check(self._lib.rq_profile_start(self._h))
+
+    def profile_stop(self) -> dict:
+        """Per-kernel-family launches, device ms, algorithmic flops and bytes."""
+        arr = (RQKernelStat * 16)()
+        n = C.c_int()
+        self._check(self._lib.rq_profile_stop(self._h, arr, 16, C.byref(n)))
+        return {arr[i].name.decode(): dict(launches=arr[i].launches, ms=arr[i].total_ms,
+                                           flops=arr[i].flops, bytes=arr[i].bytes)
+                for i in range(min(n.value, 16))}
 
     def target_column(self, j: int) -> np.ndarray:
         out = np.empty(1 << self.n_qubits, dtype=np.complex128)
