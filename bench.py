@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 METRIC = "f+grad+HVP evals/sec at n=16 FP64 (% HBM roofline); batched/served vs plain"
 UNIT = "evals/s"
 N_QUBITS = 16
-N_COLS = 1 << N_QUBITS
+N_COLS = 1 << N_QUBITS  # basis columns of the benchmark instance
 # FP64 peak of the GB300 ALU path: 2 DFMA (4 flops) per clock per SM x 152 SMs
 # x 2.07 GHz maximum SM clock (a DFMA probe on this part measured 1.19 TFLOP/s
 # at 1.99 GHz, i.e. the same 4 flops/clock/SM).
@@ -150,6 +150,14 @@ def cpu_oracle_rate(per_worker: int = 1, workers: int = 0, structure: int = 0, r
 
 # ----------------------------------------------------------------- our arm --
 
+def make_workload(args, structure: int):
+    """The benchmark instance; --sites/--depth only shrink it for profiling."""
+    import workloads as w
+    if args.sites == 8 and args.depth == 11:
+        return w.config_problem("n16", structure=structure)
+    return w.make_problem(args.sites, args.depth, 0.5, seed=1601, structure=structure)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -170,16 +178,17 @@ def run_ours(args):
     import workloads as w
     from paper_2506_23775_gb300 import rq
 
-    stream = torch.cuda.current_stream()
     dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)   # the library runs on this stream; events are recorded on it
 
     def measure(structure: int, steps: int, warmup: int, tile: int):
-        prob = w.config_problem("n16", structure=structure)
+        prob = make_workload(args, structure)
         X = w.random_directions(prob.n_params, 1, 1602)
         ctx = rq.Context(local, stream=stream.cuda_stream).setup_problem(prob)
         if tile:
             ctx.set_tile(tile, 1)
-        ctx.set_columns(0, min(N_COLS, 512 if not tile else tile))
+        ncols = 1 << prob.n
+        ctx.set_columns(0, min(ncols, 512 if not tile else tile))
         B = ctx.info()["columns_per_tile"]
         batch = B if structure == 0 else 2 * B      # parity: one even + one odd tile per batch
         gates = torch.from_numpy(prob.gates.copy()).to(dev)
@@ -189,8 +198,8 @@ def run_ours(args):
         hv_t = torch.zeros_like(dirs)
 
         def batch_range(s):
-            c0 = ((rank * (steps + warmup) + s) * batch) % N_COLS
-            return c0, c0 + batch
+            c0 = ((rank * (steps + warmup) + s) * batch) % ncols
+            return c0, min(c0 + batch, ncols)
 
         def step(s):
             ctx.set_columns(*batch_range(s))
@@ -221,7 +230,7 @@ def run_ours(args):
         if world > 1:
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_max = float(t.item())
-        value = world * steps * batch / N_COLS / (ms_max * 1e-3)
+        value = world * steps * batch / ncols / (ms_max * 1e-3)
 
         # end to end through the host C-ABI call: pinned host inputs/outputs
         g_h = torch.from_numpy(prob.gates.copy()).pin_memory().numpy()
@@ -238,7 +247,7 @@ def run_ours(args):
         tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * e2e_steps * batch / N_COLS / float(tt.item()), "unit": UNIT,
+        e2e = {"value": world * e2e_steps * batch / ncols / float(tt.item()), "unit": UNIT,
                "h2d_bytes_per_step": int(g_h.nbytes + d_h.nbytes),
                "d2h_bytes_per_step": int(8 + rg_h.nbytes + hv_h.nbytes)}
         info = ctx.info()
@@ -336,6 +345,8 @@ def main():
     ap.add_argument("--tile", type=int, default=0, help="columns per tile (power of two; 0 = automatic)")
     ap.add_argument("--general-only", action="store_true", help="skip the parity-gate measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--sites", type=int, default=8, help="chain sites (n = 2 * sites); profiling cases only")
+    ap.add_argument("--depth", type=int, default=11, help="brickwall layers; profiling cases only")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -190,3 +190,20 @@ def test_device_pointer_variants_match_host(rq):
     assert tf.item() == f
     assert np.array_equal(trg.cpu().numpy(), g)
     assert np.array_equal(thv.cpu().numpy(), hv)
+
+
+def test_tied_parity_twelve_qubits_full_basis_golden(rq):
+    # every one of the 4096 columns, against values the oracle wrote once
+    # (tests/golden/make_golden.py)
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "tied12_full_basis.json")
+    data = json.load(open(path))
+    cplx = lambda d: (np.array(d["re"]) + 1j * np.array(d["im"])).reshape(d["shape"])
+    prob = w.config_problem("tied12")
+    X = w.random_directions(prob.n_params, 1, data["direction_seed"])
+    ctx = _ctx(rq, prob)
+    f, g, hv = ctx.hvp(prob.gates, X)
+    assert abs(f - data["f"]) <= 1e-12 * abs(data["f"])
+    assert_close(g, cplx(data["rgrad"]), 12, what="rgrad")
+    assert_close(hv, cplx(data["hvp"]), 12, what="hvp")
