@@ -467,7 +467,10 @@ rq_status build_target(rq_ctx *ctx) {
 }
 
 // One evaluation over the column range; every pointer is device memory.
-rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, bool want_env,
+// env_mode: 0 no gradient environments (cost, or HVPs whose Riemannian
+// correction is not needed), 1 accumulate them, 2 reuse the accumulators of the
+// previous evaluation at the same gates (the HVPs of one tCG solve).
+rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, int env_mode,
                    double *f_out, double *rgrad, double *hvps) {
     if (!ctx->ready) return fail(ctx, RQ_ESTATE, "no target set up (call rq_setup_target first)");
     if (k < 0) return fail(ctx, RQ_EINVAL, "k = %d < 0", k);
@@ -491,7 +494,9 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                                 ctx->structure, s);
         RQ_LAUNCHED();
     }
-    RQ_CUDA(cudaMemsetAsync(ctx->d_env, 0, sizeof(double) * g * rq::kEnvDoubles, s));
+    if (k > 0 && env_mode == 0) env_mode = 1;  // the HVP correction needs the gradient environments
+    const bool want_env = env_mode == 1;
+    if (env_mode != 2) RQ_CUDA(cudaMemsetAsync(ctx->d_env, 0, sizeof(double) * g * rq::kEnvDoubles, s));
     if (k > 0) RQ_CUDA(cudaMemsetAsync(ctx->d_envd, 0, sizeof(double) * (size_t)k * g * rq::kEnvDoubles, s));
     RQ_CUDA(cudaMemsetAsync(ctx->d_facc, 0, sizeof(double), s));
 
@@ -650,9 +655,9 @@ rq_status eval_host(rq_ctx *ctx, const double *gates, const double *dirs, int k,
     if (k > 0) RQ_CUDA(cudaMemcpyAsync(ctx->d_dirs_raw, dirs, sizeof(double) * gsz * k, cudaMemcpyHostToDevice, s));
     double *o_f = ctx->d_out, *o_g = ctx->d_out + 2, *o_h = ctx->d_out + 2 + gsz;
     RQ_TRY(eval_dev(ctx, reinterpret_cast<const double *>(ctx->d_in_gates),
-                    reinterpret_cast<const double *>(ctx->d_dirs_raw), k, want_env != 0, o_f, o_g, o_h));
+                    reinterpret_cast<const double *>(ctx->d_dirs_raw), k, want_env, o_f, o_g, o_h));
     if (f) RQ_CUDA(cudaMemcpyAsync(f, o_f, sizeof(double), cudaMemcpyDeviceToHost, s));
-    if (rgrad && want_env) RQ_CUDA(cudaMemcpyAsync(rgrad, o_g, sizeof(double) * gsz, cudaMemcpyDeviceToHost, s));
+    if (rgrad && want_env == 1) RQ_CUDA(cudaMemcpyAsync(rgrad, o_g, sizeof(double) * gsz, cudaMemcpyDeviceToHost, s));
     if (hvps && k > 0) RQ_CUDA(cudaMemcpyAsync(hvps, o_h, sizeof(double) * gsz * k, cudaMemcpyDeviceToHost, s));
     RQ_CUDA(cudaStreamSynchronize(s));
     return RQ_OK;
@@ -819,18 +824,18 @@ rq_status rq_hvp(rq_ctx *ctx, const double *gates, const double *dirs, int k, do
 
 rq_status rq_cost_dev(rq_ctx *ctx, const double *gates, double *f) {
     if (!ctx) return RQ_EINVAL;
-    return eval_dev(ctx, gates, nullptr, 0, false, f, nullptr, nullptr);
+    return eval_dev(ctx, gates, nullptr, 0, 0, f, nullptr, nullptr);
 }
 
 rq_status rq_grad_dev(rq_ctx *ctx, const double *gates, double *f, double *rgrad) {
     if (!ctx) return RQ_EINVAL;
-    return eval_dev(ctx, gates, nullptr, 0, true, f, rgrad, nullptr);
+    return eval_dev(ctx, gates, nullptr, 0, 1, f, rgrad, nullptr);
 }
 
 rq_status rq_hvp_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, double *f, double *rgrad,
                      double *hvps) {
     if (!ctx) return RQ_EINVAL;
-    return eval_dev(ctx, gates, dirs, k, true, f, rgrad, hvps);
+    return eval_dev(ctx, gates, dirs, k, 1, f, rgrad, hvps);
 }
 
 rq_status rq_target_column(rq_ctx *ctx, int64_t j, double *out) {

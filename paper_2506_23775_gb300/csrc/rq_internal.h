@@ -105,7 +105,9 @@ void launch_geometry(const double2 *gates, const double2 *dirs, const double *en
                      double2 *hvps, cudaStream_t s);
 
 // Host-memory evaluation (rq_api.cu): copies inputs in and outputs out and
-// synchronises; want_env = 0 skips the gradient environments.
+// synchronises.  want_env: 0 no gradient environments, 1 accumulate them,
+// 2 reuse those of the previous evaluation at the same gates (HVPs need them
+// for the Riemannian correction).
 rq_status eval_host(rq_ctx *ctx, const double *gates, const double *dirs, int k, int want_env, double *f,
                     double *rgrad, double *hvps);
 rq_status set_error(rq_ctx *ctx, rq_status code, const char *msg);

@@ -129,7 +129,8 @@ extern "C" rq_status rq_tr_step(rq_ctx *ctx, double *gates, rq_tr_state *st) {
     for (j = 0; j < max_inner; ++j) {
         if (rr == 0.0) { code = 0; break; }
         double fh = 0.0;
-        s = rq::eval_host(ctx, gates, delta.data(), 1, 0, &fh, nullptr, Hd.data());
+        // the gradient environments at these gates are still in the accumulators
+        s = rq::eval_host(ctx, gates, delta.data(), 1, 2, &fh, nullptr, Hd.data());
         if (s != RQ_OK) return s;
         const double dHd = dot(delta, Hd);
         auto to_boundary = [&]() {
