@@ -188,6 +188,29 @@ rq_status rq_target_column(rq_ctx *ctx, int64_t j, double *out);
 /* Sizes and counters of the context. */
 rq_status rq_get_info(const rq_ctx *ctx, rq_info_t *info);
 
+/* Cost without allocation.  The paper has no counterpart: this entry point
+ * exists for callers that cannot let a library call cudaMalloc while they
+ * run -- a process whose device memory is all reserved by its own pool
+ * allocator, or a latency-critical loop that must not issue cudaMalloc /
+ * cudaFree because those calls synchronise the whole device.
+ *
+ * rq_cost_static computes the same f(G) as rq_cost over the context's column
+ * range (host `gates` [n_params][4][4] complex128 in, host `f` out; the call
+ * synchronises the context stream) but allocates nothing: all its scratch
+ * lives in one file-scope device array of RQ_STATIC_SCRATCH_BYTES that every
+ * GPU loading the library holds until the process exits.  A problem whose
+ * single column does not fit (two state tiles of 2^n, or 2^(n-1) for parity
+ * gates, complex128 amplitudes plus gate and column tables) is rejected with
+ * RQ_EINVAL and a message naming the limit; larger column ranges are swept in
+ * tiles of at most 256 columns.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current) and
+ * caches it; make that first call before any stream capture.  Every call,
+ * from any context on the device, shares the array and finds the previous
+ * call's contents there (each call clears what must start at zero); calls
+ * whose GPU work overlaps race on it and give wrong results. */
+#define RQ_STATIC_SCRATCH_BYTES (16u << 20)
+rq_status rq_cost_static(rq_ctx *ctx, const double *gates, double *f);
+
 /* Per-kernel timing of one context (benchmarking and roofline accounting).
  * Between rq_profile_start and rq_profile_stop every kernel the context
  * launches is bracketed by CUDA events on the context stream.  One record per

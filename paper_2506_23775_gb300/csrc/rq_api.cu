@@ -665,6 +665,24 @@ rq_status eval_host(rq_ctx *ctx, const double *gates, const double *dirs, int k,
 
 rq_status set_error(rq_ctx *ctx, rq_status code, const char *msg) { return fail(ctx, code, "%s", msg); }
 
+CtxView ctx_view(const rq_ctx *ctx) {
+    CtxView v{};
+    v.ready = ctx->ready;
+    v.device = ctx->device;
+    v.n = ctx->n;
+    v.g = ctx->g;
+    v.P = ctx->P;
+    v.structure = ctx->structure;
+    v.sms = ctx->sms;
+    v.n_store = ctx->n_store;
+    v.c0 = ctx->c0;
+    v.c1 = ctx->c1;
+    v.geo = ctx->geo.data();
+    v.stream = ctx->stream;
+    v.target = target_dev(ctx);
+    return v;
+}
+
 }  // namespace rq
 
 // ------------------------------------------------------------------ C ABI --

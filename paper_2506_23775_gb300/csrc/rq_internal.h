@@ -112,6 +112,17 @@ rq_status eval_host(rq_ctx *ctx, const double *gates, const double *dirs, int k,
                     double *rgrad, double *hvps);
 rq_status set_error(rq_ctx *ctx, rq_status code, const char *msg);
 
+// Read-only view of a set-up context for entry points outside rq_api.cu.
+struct CtxView {
+    bool ready;
+    int device, n, g, P, structure, sms;
+    long long n_store, c0, c1;
+    const GateGeom *geo;
+    cudaStream_t stream;
+    TargetDev target;
+};
+CtxView ctx_view(const rq_ctx *ctx);
+
 // Host helpers.
 int polar_unitary_4x4(const double *A, double *Q);    // rq_tr.cpp; 32 doubles in/out, 0 on success
 double bessel_j_table(double x, int kmax, std::vector<double> &out);  // rq_target.cu; J_0..J_kmax(x)

@@ -22,7 +22,7 @@ RQ_OK, RQ_EINVAL, RQ_ENOMEM, RQ_ECUDA, RQ_ETIMEOUT, RQ_ESTATE = 0, -1, -2, -3, -
 EXPORTS = ("rq_create", "rq_destroy", "rq_setup_target", "rq_set_columns", "rq_set_tile",
            "rq_cost", "rq_grad", "rq_hvp", "rq_cost_dev", "rq_grad_dev", "rq_hvp_dev",
            "rq_tr_step", "rq_target_column", "rq_get_info", "rq_profile_start", "rq_profile_stop",
-           "rq_last_error")
+           "rq_cost_static", "rq_last_error")
 
 
 class RQCircuit(C.Structure):
@@ -89,6 +89,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "rq_target_column": ([vp, i64, dp], C.c_int),
         "rq_get_info": ([vp, C.POINTER(RQInfo)], C.c_int),
         "rq_profile_start": ([vp], C.c_int),
+        "rq_cost_static": ([vp, dp, dp], C.c_int),
         "rq_profile_stop": ([vp, C.POINTER(RQKernelStat), C.c_int, C.POINTER(C.c_int)], C.c_int),
         "rq_last_error": ([vp], C.c_char_p),
     }
@@ -214,6 +215,14 @@ class Context:
                                      d.shape[0], C.byref(f), _dptr(rg.view(np.float64)),
                                      _dptr(hv.view(np.float64))))
         return f.value, rg, hv
+
+    def cost_static(self, gates) -> float:
+        """``f`` like :meth:`cost`, with no device allocation in the call
+        (scratch in the library's fixed static device array)."""
+        g = _c128(gates)
+        f = C.c_double()
+        self._check(self._lib.rq_cost_static(self._h, _dptr(g.view(np.float64)), C.byref(f)))
+        return f.value
 
     # --- evaluations (device pointers, stream ordered) ---------------------
     def cost_dev(self, gates_ptr: int, f_ptr: int):
