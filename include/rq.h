@@ -149,6 +149,19 @@ rq_status rq_set_columns(rq_ctx *ctx, int64_t col_begin, int64_t col_end);
  * workspace; RQ_ENOMEM if it does not fit. */
 rq_status rq_set_tile(rq_ctx *ctx, int columns_per_tile, int max_dirs);
 
+/* Output space of rq_grad / rq_hvp (and their _dev variants).
+ * RQ_SPACE_RIEMANNIAN (default): grad f = P_G(gbar) (Eq. grad_proj) and
+ * Hess f(G)[X] (Eq. hessian_def) with X projected onto the tangent space.
+ * RQ_SPACE_EUCLIDEAN: the cost extended to all complex 4x4 matrices (as an
+ * autograd framework sees it): gbar = d_x f + i d_y f (Eq. def_grad, tied
+ * copies summed) and the Euclidean Hessian applied to the raw direction,
+ * Dgbar[X] = d/de gbar(G + e X) at e = 0; for parity circuits both are masked
+ * to the pattern of Eq. paritygatematrix.  rq_tr_step always works in the
+ * Riemannian space.  RQ_EINVAL for any other value. */
+#define RQ_SPACE_RIEMANNIAN 0
+#define RQ_SPACE_EUCLIDEAN 1
+rq_status rq_set_gradient_space(rq_ctx *ctx, int space);
+
 /* f(G) over the column range (Eq. f_target_sum_unit_vec).  gates: host
  * [n_params][4][4] complex128; f: host double. */
 rq_status rq_cost(rq_ctx *ctx, const double *gates, double *f);

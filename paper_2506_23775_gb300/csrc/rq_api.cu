@@ -70,6 +70,7 @@ struct rq_ctx {
     long long problem_bytes = 0, work_bytes = 0, small_bytes = 0;
     long long launches = 0;
     long long cols_cap = 0;
+    int space = 0;  // 0 Riemannian outputs, 1 Euclidean (rq_set_gradient_space)
     // per-kernel profiling (events bracket every launch while enabled)
     struct ProfRec {
         int family;
@@ -491,7 +492,7 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
     if (k > 0) {
         ProfScope ps(ctx, kFamGeometry, 0.0, 2.0 * k * P * 16 * sizeof(double2));
         rq::launch_project_dirs(ctx->d_gates, reinterpret_cast<const double2 *>(dirs), ctx->d_dirs, P, k,
-                                ctx->structure, s);
+                                ctx->structure, ctx->space, s);
         RQ_LAUNCHED();
     }
     if (k > 0 && env_mode == 0) env_mode = 1;  // the HVP correction needs the gradient environments
@@ -626,7 +627,7 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
     {
         ProfScope ps(ctx, kFamGeometry, 0.0, 0.0);
         rq::launch_geometry(ctx->d_gates, ctx->d_dirs, ctx->d_env, ctx->d_envd, ctx->d_param_of, g, P, k,
-                            ctx->structure, ctx->d_facc, f_out,
+                            ctx->structure, ctx->space, ctx->d_facc, f_out,
                             want_env ? reinterpret_cast<double2 *>(rgrad) : nullptr,
                             reinterpret_cast<double2 *>(hvps), s);
     }
@@ -664,6 +665,8 @@ rq_status eval_host(rq_ctx *ctx, const double *gates, const double *dirs, int k,
 }
 
 rq_status set_error(rq_ctx *ctx, rq_status code, const char *msg) { return fail(ctx, code, "%s", msg); }
+
+int gradient_space(const rq_ctx *ctx) { return ctx->space; }
 
 CtxView ctx_view(const rq_ctx *ctx) {
     CtxView v{};
@@ -822,6 +825,14 @@ rq_status rq_set_tile(rq_ctx *ctx, int columns_per_tile, int max_dirs) {
     ctx->user_B = columns_per_tile;
     ctx->user_kc = max_dirs;
     return rebuild_tiles(ctx);
+}
+
+rq_status rq_set_gradient_space(rq_ctx *ctx, int space) {
+    if (!ctx) return RQ_EINVAL;
+    if (space != RQ_SPACE_RIEMANNIAN && space != RQ_SPACE_EUCLIDEAN)
+        return fail(ctx, RQ_EINVAL, "space %d is neither RQ_SPACE_RIEMANNIAN nor RQ_SPACE_EUCLIDEAN", space);
+    ctx->space = space;
+    return RQ_OK;
 }
 
 rq_status rq_cost(rq_ctx *ctx, const double *gates, double *f) {

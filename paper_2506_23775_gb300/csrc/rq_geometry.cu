@@ -8,6 +8,8 @@
 //   parity-conserving gates keep only their pattern (Eq. paritygatematrix).
 // * Riemannian gradient grad f = G skew(G^dagger gbar) (Eq. proj_tangent,
 //   Eq. grad_proj).
+// * With the Euclidean output option the masked gbar and Dgbar[X] (X a raw
+//   complex direction, only masked) are returned instead (autograd use).
 // * Riemannian Hessian along a tangent X (Eq. vector_field_derivative,
 //   Eq. hessian_def): differentiating xi(V) = V skew(V^dagger gbar(V)) and
 //   projecting gives, with X = G Omega and Omega skew-Hermitian,
@@ -102,12 +104,12 @@ __global__ void k_reduce_f(const double *fpart, int B, double *facc) {
 }
 
 __global__ void k_project_dirs(const double2 *gates, const double2 *raw, double2 *out, int P, int k,
-                               int structure) {
+                               int structure, int euclidean) {
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= P * k) return;
     const int p = id % P;
     M4 G = load4(gates + (long long)p * 16);
-    M4 X = project(G, load4(raw + (long long)id * 16));
+    M4 X = euclidean ? load4(raw + (long long)id * 16) : project(G, load4(raw + (long long)id * 16));
     apply_mask(X, structure);
     for (int i = 0; i < 16; ++i) out[(long long)id * 16 + i] = X.a[i];
 }
@@ -121,7 +123,7 @@ __global__ void k_mask_gates(const double2 *in, double2 *out, int P, int structu
 // Thread per (direction slot d in [0, k], parameter p); slot 0 = gradient.
 __global__ void k_geometry(const double2 *gates, const double2 *dirs, const double *env,
                            const double *env_dot, const int32_t *param_of, int g, int P, int k,
-                           int structure, const double *facc, double *f_out, double2 *rgrad,
+                           int structure, int euclidean, const double *facc, double *f_out, double2 *rgrad,
                            double2 *hvps) {
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id == 0 && f_out != nullptr) f_out[0] = facc[0];
@@ -141,7 +143,7 @@ __global__ void k_geometry(const double2 *gates, const double2 *dirs, const doub
     apply_mask(gb, structure);
     if (d == 0) {
         if (rgrad == nullptr) return;
-        const M4 R = project(G, gb);
+        const M4 R = euclidean ? gb : project(G, gb);
         for (int i = 0; i < 16; ++i) rgrad[(long long)p * 16 + i] = R.a[i];
         return;
     }
@@ -157,6 +159,11 @@ __global__ void k_geometry(const double2 *gates, const double2 *dirs, const doub
         }
     }
     apply_mask(dg, structure);
+    if (euclidean) {  // Euclidean Hessian applied to the direction: Dgbar[X]
+        if (hvps == nullptr) return;
+        for (int i = 0; i < 16; ++i) hvps[((long long)dd * P + p) * 16 + i] = dg.a[i];
+        return;
+    }
     const M4 X = load4(dirs + ((long long)dd * P + p) * 16);
     const M4 XS = matmul(X, herm_part(matmul_dag(G, gb), +1.0));
     for (int i = 0; i < 16; ++i) dg.a[i] = make_double2(dg.a[i].x - XS.a[i].x, dg.a[i].y - XS.a[i].y);
@@ -176,10 +183,10 @@ void launch_reduce_f(const double *fpart, int B, double *facc, cudaStream_t s) {
 }
 
 void launch_project_dirs(const double2 *gates, const double2 *raw, double2 *out, int n_params,
-                         int k, int structure, cudaStream_t s) {
+                         int k, int structure, int euclidean, cudaStream_t s) {
     const int n = n_params * k;
     if (n == 0) return;
-    k_project_dirs<<<(n + 63) / 64, 64, 0, s>>>(gates, raw, out, n_params, k, structure);
+    k_project_dirs<<<(n + 63) / 64, 64, 0, s>>>(gates, raw, out, n_params, k, structure, euclidean);
 }
 
 void launch_mask_gates(const double2 *in, double2 *out, int n_params, int structure, cudaStream_t s) {
@@ -189,11 +196,11 @@ void launch_mask_gates(const double2 *in, double2 *out, int n_params, int struct
 
 void launch_geometry(const double2 *gates, const double2 *dirs, const double *env,
                      const double *env_dot, const int32_t *param_of, int n_gates, int n_params,
-                     int k, int structure, const double *facc, double *f_out, double2 *rgrad,
+                     int k, int structure, int euclidean, const double *facc, double *f_out, double2 *rgrad,
                      double2 *hvps, cudaStream_t s) {
     const int n = n_params * (k + 1);
     k_geometry<<<(n + 63) / 64, 64, 0, s>>>(gates, dirs, env, env_dot, param_of, n_gates, n_params,
-                                            k, structure, facc, f_out, rgrad, hvps);
+                                            k, structure, euclidean, facc, f_out, rgrad, hvps);
 }
 
 }  // namespace rq

@@ -97,11 +97,11 @@ void launch_cheb_init(const long long *off_u, const long long *sizes, int n_sect
 void launch_reduce_env(const double *part, int ncta, int n_gates, double *env, cudaStream_t s);
 void launch_reduce_f(const double *fpart, int B, double *facc, cudaStream_t s);
 void launch_project_dirs(const double2 *gates, const double2 *raw, double2 *out, int n_params,
-                         int k, int structure, cudaStream_t s);
+                         int k, int structure, int euclidean, cudaStream_t s);
 void launch_mask_gates(const double2 *in, double2 *out, int n_params, int structure, cudaStream_t s);
 void launch_geometry(const double2 *gates, const double2 *dirs, const double *env,
                      const double *env_dot, const int32_t *param_of, int n_gates, int n_params,
-                     int k, int structure, const double *facc, double *f_out, double2 *rgrad,
+                     int k, int structure, int euclidean, const double *facc, double *f_out, double2 *rgrad,
                      double2 *hvps, cudaStream_t s);
 
 // Host-memory evaluation (rq_api.cu): copies inputs in and outputs out and
@@ -111,6 +111,7 @@ void launch_geometry(const double2 *gates, const double2 *dirs, const double *en
 rq_status eval_host(rq_ctx *ctx, const double *gates, const double *dirs, int k, int want_env, double *f,
                     double *rgrad, double *hvps);
 rq_status set_error(rq_ctx *ctx, rq_status code, const char *msg);
+int gradient_space(const rq_ctx *ctx);
 
 // Read-only view of a set-up context for entry points outside rq_api.cu.
 struct CtxView {

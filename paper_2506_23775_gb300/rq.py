@@ -22,7 +22,7 @@ RQ_OK, RQ_EINVAL, RQ_ENOMEM, RQ_ECUDA, RQ_ETIMEOUT, RQ_ESTATE = 0, -1, -2, -3, -
 EXPORTS = ("rq_create", "rq_destroy", "rq_setup_target", "rq_set_columns", "rq_set_tile",
            "rq_cost", "rq_grad", "rq_hvp", "rq_cost_dev", "rq_grad_dev", "rq_hvp_dev",
            "rq_tr_step", "rq_target_column", "rq_get_info", "rq_profile_start", "rq_profile_stop",
-           "rq_cost_static", "rq_last_error")
+           "rq_cost_static", "rq_set_gradient_space", "rq_last_error")
 
 
 class RQCircuit(C.Structure):
@@ -90,6 +90,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "rq_get_info": ([vp, C.POINTER(RQInfo)], C.c_int),
         "rq_profile_start": ([vp], C.c_int),
         "rq_cost_static": ([vp, dp, dp], C.c_int),
+        "rq_set_gradient_space": ([vp, C.c_int], C.c_int),
         "rq_profile_stop": ([vp, C.POINTER(RQKernelStat), C.c_int, C.POINTER(C.c_int)], C.c_int),
         "rq_last_error": ([vp], C.c_char_p),
     }
@@ -121,6 +122,8 @@ class Context:
         if st != RQ_OK:
             raise RQError(st, self._lib.rq_last_error(None).decode())
         self._h = h
+        self._stream = stream or None
+        self._space = 0
         self.n_params = 0
         self.n_qubits = 0
 
@@ -170,6 +173,15 @@ class Context:
         """Set up from a ``workloads.Problem``."""
         return self.setup(prob.L, prob.pairs, prob.param_of, prob.n_params, prob.structure,
                           prob.J, prob.U, prob.t, prob.periodic)
+
+    def set_gradient_space(self, space: int):
+        """0: Riemannian outputs (default); 1: Euclidean gradient and Hessian."""
+        self._check(self._lib.rq_set_gradient_space(self._h, int(space)))
+        self._space = int(space)
+
+    def stream_handle(self):
+        """The cudaStream_t given at creation (None: a library-owned stream)."""
+        return self._stream
 
     def set_columns(self, begin: int, end: int):
         self._check(self._lib.rq_set_columns(self._h, int(begin), int(end)))
