@@ -224,6 +224,33 @@ rq_status rq_get_info(const rq_ctx *ctx, rq_info_t *info);
 #define RQ_STATIC_SCRATCH_BYTES (16u << 20)
 rq_status rq_cost_static(rq_ctx *ctx, const double *gates, double *f);
 
+/* Batches of independent problems (uneven n, depth, t, U; paper Sec.
+ * "Parallelization": the basis sums of different problems are independent).
+ * Every problem has its own context (target blocks, workspace, stream).  One
+ * evaluation of the whole batch is one CUDA-graph launch whose branches run
+ * the problems concurrently; results are bitwise those of each problem
+ * evaluated alone.  The columns-per-tile of the batch is autotuned at the
+ * first evaluation (rq_batch_set_tile(b, 0)) or fixed (power of two).
+ *
+ * rq_batch_hvp: host arrays.  gates: every problem's [n_params][4][4]
+ * complex128 concatenated in the order of rq_batch_add; dirs: for each
+ * problem [k][n_params][4][4], concatenated the same way; f: [n_problems];
+ * rgrad: same layout as gates; hvps: same layout as dirs (Riemannian
+ * quantities as in rq_hvp; NULL outputs are skipped).  plain = 1 evaluates
+ * the problems one after another without the graph (for comparison).
+ * Synchronises.  rq_batch_info: problem count, chosen tile, and the
+ * autotuner's timings (ms per cost-only batch evaluation for tile caps 64,
+ * 128, 256, 512; -1 where the cap did not fit). */
+typedef struct rq_batch rq_batch;
+rq_status rq_batch_create(rq_batch **out, int device);
+rq_status rq_batch_destroy(rq_batch *b);
+rq_status rq_batch_add(rq_batch *b, const rq_target *target, const rq_circuit *circuit, int *index);
+rq_status rq_batch_set_tile(rq_batch *b, int columns_per_tile);
+rq_status rq_batch_hvp(rq_batch *b, const double *gates, const double *dirs, int k, int plain, double *f,
+                       double *rgrad, double *hvps);
+rq_status rq_batch_info(const rq_batch *b, int *n_problems, int *columns_per_tile, double *tune_ms);
+const char *rq_batch_last_error(const rq_batch *b);
+
 /* Per-kernel timing of one context (benchmarking and roofline accounting).
  * Between rq_profile_start and rq_profile_stop every kernel the context
  * launches is bracketed by CUDA events on the context stream.  One record per

@@ -668,6 +668,19 @@ rq_status set_error(rq_ctx *ctx, rq_status code, const char *msg) { return fail(
 
 int gradient_space(const rq_ctx *ctx) { return ctx->space; }
 
+rq_status eval_device(rq_ctx *ctx, const double *gates, const double *dirs, int k, int env_mode, double *f,
+                      double *rgrad, double *hvps) {
+    return eval_dev(ctx, gates, dirs, k, env_mode, f, rgrad, hvps);
+}
+
+rq_status prepare_capacity(rq_ctx *ctx, int k) { return ensure_small(ctx, k); }
+
+cudaStream_t ctx_stream(const rq_ctx *ctx) { return ctx->stream; }
+
+long long workspace_bytes_for(const rq_ctx *ctx, int columns_per_tile, int kc) {
+    return (long long)columns_per_tile * bytes_per_column(ctx, kc);
+}
+
 CtxView ctx_view(const rq_ctx *ctx) {
     CtxView v{};
     v.ready = ctx->ready;

@@ -112,6 +112,13 @@ rq_status eval_host(rq_ctx *ctx, const double *gates, const double *dirs, int k,
                     double *rgrad, double *hvps);
 rq_status set_error(rq_ctx *ctx, rq_status code, const char *msg);
 int gradient_space(const rq_ctx *ctx);
+// Device-pointer evaluation on the context stream (capturable once the
+// context's small buffers hold k directions: prepare_capacity first).
+rq_status eval_device(rq_ctx *ctx, const double *gates, const double *dirs, int k, int env_mode, double *f,
+                      double *rgrad, double *hvps);
+rq_status prepare_capacity(rq_ctx *ctx, int k);
+cudaStream_t ctx_stream(const rq_ctx *ctx);
+long long workspace_bytes_for(const rq_ctx *ctx, int columns_per_tile, int kc);
 
 // Read-only view of a set-up context for entry points outside rq_api.cu.
 struct CtxView {

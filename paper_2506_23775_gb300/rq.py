@@ -22,7 +22,9 @@ RQ_OK, RQ_EINVAL, RQ_ENOMEM, RQ_ECUDA, RQ_ETIMEOUT, RQ_ESTATE = 0, -1, -2, -3, -
 EXPORTS = ("rq_create", "rq_destroy", "rq_setup_target", "rq_set_columns", "rq_set_tile",
            "rq_cost", "rq_grad", "rq_hvp", "rq_cost_dev", "rq_grad_dev", "rq_hvp_dev",
            "rq_tr_step", "rq_target_column", "rq_get_info", "rq_profile_start", "rq_profile_stop",
-           "rq_cost_static", "rq_set_gradient_space", "rq_last_error")
+           "rq_cost_static", "rq_set_gradient_space", "rq_batch_create", "rq_batch_destroy",
+           "rq_batch_add", "rq_batch_set_tile", "rq_batch_hvp", "rq_batch_info", "rq_batch_last_error",
+           "rq_last_error")
 
 
 class RQCircuit(C.Structure):
@@ -91,6 +93,13 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "rq_profile_start": ([vp], C.c_int),
         "rq_cost_static": ([vp, dp, dp], C.c_int),
         "rq_set_gradient_space": ([vp, C.c_int], C.c_int),
+        "rq_batch_create": ([C.POINTER(vp), C.c_int], C.c_int),
+        "rq_batch_destroy": ([vp], C.c_int),
+        "rq_batch_add": ([vp, C.POINTER(RQTarget), C.POINTER(RQCircuit), C.POINTER(C.c_int)], C.c_int),
+        "rq_batch_set_tile": ([vp, C.c_int], C.c_int),
+        "rq_batch_hvp": ([vp, dp, dp, C.c_int, C.c_int, dp, dp, dp], C.c_int),
+        "rq_batch_info": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int), dp], C.c_int),
+        "rq_batch_last_error": ([vp], C.c_char_p),
         "rq_profile_stop": ([vp, C.POINTER(RQKernelStat), C.c_int, C.POINTER(C.c_int)], C.c_int),
         "rq_last_error": ([vp], C.c_char_p),
     }
@@ -278,3 +287,74 @@ def tr_state(radius=0.01, max_radius=0.1, rho_accept=0.125, kappa=0.1, theta=1.0
     s.radius, s.max_radius, s.rho_accept = radius, max_radius, rho_accept
     s.kappa, s.theta, s.max_inner = kappa, theta, max_inner
     return s
+
+
+class Batch:
+    """Independent problems evaluated together (one CUDA-graph launch)."""
+
+    def __init__(self, device: int = 0):
+        self._lib = load()
+        h = C.c_void_p()
+        st = self._lib.rq_batch_create(C.byref(h), device)
+        if st != RQ_OK:
+            raise RQError(st, "rq_batch_create failed")
+        self._h = h
+        self.n_params = []
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rq_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != RQ_OK:
+            raise RQError(st, self._lib.rq_batch_last_error(self._h).decode())
+
+    def add_problem(self, prob) -> int:
+        pairs = np.ascontiguousarray(prob.pairs, dtype=np.int32)
+        pof = np.ascontiguousarray(prob.param_of, dtype=np.int32)
+        circ = RQCircuit(prob.n, pairs.shape[0], prob.n_params, prob.structure,
+                         pairs.ctypes.data_as(C.POINTER(C.c_int32)), pof.ctypes.data_as(C.POINTER(C.c_int32)))
+        tgt = RQTarget(0, prob.L, 1 if prob.periodic else 0, prob.J, prob.U, prob.t)
+        idx = C.c_int()
+        self._check(self._lib.rq_batch_add(self._h, C.byref(tgt), C.byref(circ), C.byref(idx)))
+        self.n_params.append(prob.n_params)
+        return idx.value
+
+    def set_tile(self, columns_per_tile: int):
+        self._check(self._lib.rq_batch_set_tile(self._h, int(columns_per_tile)))
+
+    def info(self) -> dict:
+        n, t = C.c_int(), C.c_int()
+        ms = (C.c_double * 4)()
+        self._check(self._lib.rq_batch_info(self._h, C.byref(n), C.byref(t), ms))
+        return {"n_problems": n.value, "columns_per_tile": t.value,
+                "tune_ms": dict(zip((64, 128, 256, 512), list(ms)))}
+
+    def hvp(self, gates_list, dirs_list, plain: bool = False):
+        """Per-problem lists in, per-problem (f, rgrad, hvps) lists out."""
+        k = dirs_list[0].shape[0] if dirs_list else 0
+        g = np.ascontiguousarray(np.concatenate([np.asarray(x, np.complex128).ravel() for x in gates_list]))
+        d = np.ascontiguousarray(np.concatenate([np.asarray(x, np.complex128).ravel() for x in dirs_list])) \
+            if k else np.zeros(1, np.complex128)
+        f = np.empty(len(gates_list))
+        rg = np.empty_like(g)
+        hv = np.empty_like(d)
+        self._check(self._lib.rq_batch_hvp(self._h, _dptr(g.view(np.float64)), _dptr(d.view(np.float64)), k,
+                                           1 if plain else 0, _dptr(f), _dptr(rg.view(np.float64)),
+                                           _dptr(hv.view(np.float64)) if k else None))
+        out, go, do = [], 0, 0
+        for P in self.n_params:
+            r = rg[go:go + P * 16].reshape(P, 4, 4)
+            h = hv[do:do + k * P * 16].reshape(k, P, 4, 4) if k else None
+            out.append((r, h))
+            go += P * 16
+            do += k * P * 16
+        return f, [o[0] for o in out], [o[1] for o in out]
