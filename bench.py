@@ -255,10 +255,45 @@ def run_ours(args):
         return dict(value=value, ms_per_step=ms_max / steps, launches=launches, prof=prof, clocks=clk.summary(),
                     e2e=e2e, batch=batch, B=B, info=info)
 
+    def measure_batched():
+        """256 independent problems (n in {8,10,12}, depth in {3,5,7,9}, t ~ U[0.1,1],
+        U ~ U[2,8], seed 301): f + grad + 1 HVP of every problem, as one CUDA-graph
+        launch (batched) and one problem after another (plain)."""
+        probs = w.batch_problems(256, seed=301)
+        b = rq.Batch(local)
+        t0 = time.perf_counter()
+        for p in probs:
+            b.add_problem(p)
+        setup_s = time.perf_counter() - t0
+        gates = [p.gates for p in probs]
+        dirs = [w.random_directions(p.n_params, 1, 3000 + i) for i, p in enumerate(probs)]
+        t0 = time.perf_counter()
+        b.hvp(gates, dirs)                      # autotune + capture + first replay
+        first_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        fb, _, _ = b.hvp(gates, dirs)
+        batched_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        fp, _, _ = b.hvp(gates, dirs, plain=True)
+        plain_s = time.perf_counter() - t0
+        info = b.info()
+        b.close()
+        flops = sum(9 * p.n_gates * 32.0 * 4 ** p.n for p in probs)
+        return {"problems": len(probs), "unit": "problem evals/s",
+                "batched": len(probs) / batched_s, "plain": len(probs) / plain_s,
+                "speedup": plain_s / batched_s, "batched_s": batched_s, "plain_s": plain_s,
+                "bitwise_equal": bool(np.array_equal(fb, fp)), "columns_per_tile": info["columns_per_tile"],
+                "autotune_ms": info["tune_ms"], "setup_s": setup_s, "first_call_s": first_s,
+                "fp64_tflops_batched": flops / batched_s / 1e12,
+                "workload": "256 problems: n in {8,10,12}, depth in {3,5,7,9}, t~U[0.1,1], U~U[2,8], "
+                            "general gates, f + grad + 1 HVP each, full basis sums (seed 301)"}
+
     gen = measure(0, args.steps, args.warmup, args.tile)
     par = None
     if not args.general_only:
         par = measure(1, args.steps, args.warmup, args.tile)
+
+    batched = measure_batched() if (args.batched and world == 1) else None
 
     if rank != 0:
         if world > 1:
@@ -300,6 +335,8 @@ def run_ours(args):
                           "columns_per_step": par["batch"], "e2e": par["e2e"], "roofline": roofline(par),
                           "gpu_launches": par["launches"], "clocks": par["clocks"],
                           "structure": "parity-conserving gates, parity-sector tiles (2^15 stored amplitudes)"}
+    if batched is not None:
+        line["batched"] = batched
     if world == 1 and not args.no_cpu:
         rates, cores, ncols = cpu_oracle_rate(per_worker=1)
         line["cpu_baseline"] = {"value": rates[0], "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -344,6 +381,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--tile", type=int, default=0, help="columns per tile (power of two; 0 = automatic)")
     ap.add_argument("--general-only", action="store_true", help="skip the parity-gate measurement")
+    ap.add_argument("--batched", action="store_true", help="also time 256 uneven problems batched vs plain")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--sites", type=int, default=8, help="chain sites (n = 2 * sites); profiling cases only")
     ap.add_argument("--depth", type=int, default=11, help="brickwall layers; profiling cases only")
