@@ -1,0 +1,224 @@
+"""Continuous-batching request loop for cost / gradient / HVP requests.
+
+Requests for problems of different sizes arrive over time.  The server admits
+a request as soon as a slot and enough device memory are free (admission by
+HBM footprint: the problem's target blocks plus its sweep workspace), queues
+its evaluation at once on that request's own CUDA stream -- so requests that
+arrive while others are on the GPU run concurrently with them -- and returns
+each result when its completion event fires.  Target blocks and workspaces
+stay on the device between requests for the same problem (a context cache),
+so repeated requests skip the set-up.
+
+Every evaluation runs the library's kernels in the same order as the same
+request evaluated alone on a context with the same tile size, so a result in
+the mix equals the result alone bit for bit.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+from math import comb
+from typing import Dict, List, Optional
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    rid: int
+    kind: str                 # "cost" | "grad" | "hvp"
+    problem: object           # workloads.Problem (topology, target parameters, gates)
+    dirs: Optional[np.ndarray] = None
+    arrival: float = 0.0      # seconds after the start of the stream
+    # filled by the server
+    admitted: float = float("nan")
+    done: float = float("nan")
+    f: float = float("nan")
+    rgrad: Optional[np.ndarray] = None
+    hvps: Optional[np.ndarray] = None
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+def problem_key(p) -> tuple:
+    return (p.L, p.periodic, p.J, p.U, p.t, p.structure, p.n_params,
+            p.pairs.tobytes(), p.param_of.tobytes())
+
+
+def footprint_bytes(p, tile: int, k: int = 1) -> int:
+    """Device bytes of a problem's context: target blocks, tables, workspace."""
+    n_store = (1 << (p.n - 1)) if p.structure == 1 else (1 << p.n)
+    target = comb(2 * p.L, p.L) ** 2 * 16 + 3 * (1 << p.n) * 4
+    sets = (1 + k) * (p.n_gates + 1) + 1 + k
+    return int(target + tile * sets * n_store * 16)
+
+
+class _Slot:
+    def __init__(self, ctx, stream, key, tile, nbytes):
+        self.ctx, self.stream, self.key, self.tile, self.nbytes = ctx, stream, key, tile, nbytes
+        self.busy = False
+        self.last_used = 0.0
+
+
+class Server:
+    """Continuous batching over per-problem device contexts.
+
+    ``memory_budget``: bytes of device memory the server may hold;
+    ``max_inflight``: evaluations on the GPU at once; ``tile``: columns per
+    tile of every context (a power of two; smaller tiles lower the footprint).
+    """
+
+    def __init__(self, device: int = 0, memory_budget: Optional[int] = None, max_inflight: int = 8,
+                 tile: int = 128):
+        import torch
+        from . import rq
+        self.torch, self.rq = torch, rq
+        self.device = device
+        self.dev = torch.device("cuda", device)
+        if memory_budget is None:
+            free, _ = torch.cuda.mem_get_info(self.dev)
+            memory_budget = int(0.5 * free)
+        self.budget = memory_budget
+        self.max_inflight = max_inflight
+        self.tile = tile
+        self.cache: "collections.OrderedDict[tuple, _Slot]" = collections.OrderedDict()
+        self.held = 0
+        self.stats = collections.Counter()
+
+    # -- contexts ----------------------------------------------------------
+    def _evict_idle(self, need: int) -> bool:
+        for key in list(self.cache.keys()):
+            if self.held + need <= self.budget:
+                return True
+            s = self.cache[key]
+            if not s.busy:
+                s.ctx.close()
+                self.held -= s.nbytes
+                del self.cache[key]
+                self.stats["evicted"] += 1
+        return self.held + need <= self.budget
+
+    def _slot_for(self, req: Request) -> Optional[_Slot]:
+        p = req.problem
+        key = problem_key(p)
+        s = self.cache.get(key)
+        if s is not None:
+            if s.busy:
+                return None                   # one evaluation per context at a time
+            self.cache.move_to_end(key)
+            self.stats["reused"] += 1
+            return s
+        tile = min(self.tile, 1 << p.n)
+        k = 0 if req.dirs is None else req.dirs.shape[0]
+        need = footprint_bytes(p, tile, max(k, 1))
+        if need > self.budget:
+            raise MemoryError(f"request {req.rid} needs {need} bytes, the budget is {self.budget}")
+        if not self._evict_idle(need):
+            return None
+        stream = self.torch.cuda.Stream(device=self.dev)
+        ctx = self.rq.Context(self.device, stream=stream.cuda_stream).setup_problem(p)
+        ctx.set_tile(tile, 1)
+        s = _Slot(ctx, stream, key, tile, need)
+        self.cache[key] = s
+        self.held += need
+        self.stats["setups"] += 1
+        return s
+
+    # -- one evaluation, queued on the slot's stream ------------------------
+    def _launch(self, req: Request, s: _Slot):
+        torch = self.torch
+        p = req.problem
+        with torch.cuda.stream(s.stream):
+            g = torch.from_numpy(np.ascontiguousarray(p.gates)).to(self.dev, non_blocking=False)
+            f = torch.zeros(1, dtype=torch.float64, device=self.dev)
+            rg = torch.zeros_like(g)
+            if req.kind == "hvp":
+                d = torch.from_numpy(np.ascontiguousarray(req.dirs)).to(self.dev)
+                hv = torch.zeros_like(d)
+        # the library runs on the same stream, so the copies above precede its kernels
+        if req.kind == "cost":
+            s.ctx.cost_dev(g.data_ptr(), f.data_ptr())
+            out = (f, None, None)
+        elif req.kind == "grad":
+            s.ctx.grad_dev(g.data_ptr(), f.data_ptr(), rg.data_ptr())
+            out = (f, rg, None)
+        else:
+            s.ctx.hvp_dev(g.data_ptr(), d.data_ptr(), req.dirs.shape[0], f.data_ptr(), rg.data_ptr(),
+                          hv.data_ptr())
+            out = (f, rg, hv)
+        ev = torch.cuda.Event()
+        ev.record(s.stream)
+        return ev, out
+
+    def run(self, requests: List[Request], realtime: bool = True) -> Dict[str, float]:
+        """Serve ``requests`` (sorted by arrival).  ``realtime``: honour the
+        arrival times; otherwise every request is available at once."""
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        inflight = []
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0
+        waiting: List[Request] = []
+        while pending or waiting or inflight:
+            t = now()
+            while pending and (not realtime or pending[0].arrival <= t):
+                waiting.append(pending.popleft())
+            # admit as slots and memory allow (first come, first served; a
+            # request whose context is busy does not block later ones)
+            still = []
+            for req in waiting:
+                if len(inflight) >= self.max_inflight:
+                    still.append(req)
+                    continue
+                s = self._slot_for(req)
+                if s is None:
+                    still.append(req)
+                    continue
+                s.busy = True
+                req.admitted = now()
+                ev, out = self._launch(req, s)
+                inflight.append((req, s, ev, out))
+            waiting = still
+            # collect finished work
+            rest = []
+            for item in inflight:
+                req, s, ev, out = item
+                if ev.query():
+                    f, rg, hv = out
+                    req.f = float(f.item())
+                    req.rgrad = None if rg is None else rg.cpu().numpy()
+                    req.hvps = None if hv is None else hv.cpu().numpy()
+                    req.done = now()
+                    s.busy = False
+                    s.last_used = req.done
+                else:
+                    rest.append(item)
+            inflight = rest
+            if inflight or waiting or pending:
+                time.sleep(0.0005)
+        wall = now()
+        lat = np.array([r.latency for r in requests])
+        return {"requests": len(requests), "wall_s": wall, "evals_per_s": len(requests) / wall,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "setups": self.stats["setups"], "reused": self.stats["reused"], "evicted": self.stats["evicted"]}
+
+    def close(self):
+        for s in self.cache.values():
+            s.ctx.close()
+        self.cache.clear()
+        self.held = 0
+
+
+def poisson_stream(problems, kinds, rate_hz: float, seed: int, k: int = 1) -> List[Request]:
+    """Requests over ``problems`` with exponential inter-arrival times."""
+    import workloads as w
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i, (p, kind) in enumerate(zip(problems, kinds)):
+        t += rng.exponential(1.0 / rate_hz)
+        dirs = w.random_directions(p.n_params, k, seed * 1000 + i) if kind == "hvp" else None
+        out.append(Request(rid=i, kind=kind, problem=p, dirs=dirs, arrival=t))
+    return out
