@@ -34,6 +34,7 @@ N_COLS = 1 << N_QUBITS  # basis columns of the benchmark instance
 # x 2.07 GHz maximum SM clock (a DFMA probe on this part measured 1.19 TFLOP/s
 # at 1.99 GHz, i.e. the same 4 flops/clock/SM).
 FP64_PEAK_TFLOPS = 4 * 152 * 2.07e9 / 1e12
+FP32_PIPE_TOPS = 128 * 152 * 2.07e9 / 1e12   # FP32 pipe instructions per second (one FMA = one)
 HBM_FALLBACK_GBS = 6800.0
 
 WORKLOAD = ("spinful Fermi-Hubbard chain, 8 sites (n=16 qubits), open, J=1 U=4 t=0.5; "
@@ -181,10 +182,11 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)   # the library runs on this stream; events are recorded on it
 
-    def measure(structure: int, steps: int, warmup: int, tile: int):
+    def measure(structure: int, steps: int, warmup: int, tile: int, arith: int = 0):
         prob = make_workload(args, structure)
         X = w.random_directions(prob.n_params, 1, 1602)
         ctx = rq.Context(local, stream=stream.cuda_stream).setup_problem(prob)
+        ctx.set_arithmetic(arith)
         if tile:
             ctx.set_tile(tile, 1)
         ncols = 1 << prob.n
@@ -292,6 +294,11 @@ def run_ours(args):
     par = None
     if not args.general_only:
         par = measure(1, args.steps, args.warmup, args.tile)
+    df_gen = df_par = None
+    if not args.no_df64:
+        df_gen = measure(0, args.steps, args.warmup, args.tile, arith=1)
+        if not args.general_only:
+            df_par = measure(1, args.steps, args.warmup, args.tile, arith=1)
 
     batched = measure_batched() if (args.batched and world == 1) else None
 
@@ -302,12 +309,22 @@ def run_ours(args):
 
     hbm, hbm_src = _measured_hbm()
 
-    def roofline(res):
+    def roofline(res, df64=False):
         sweep = {k: v for k, v in res["prof"].items() if k.startswith(("fwd", "bwd"))}
         dom = max(sweep, key=lambda k: sweep[k]["ms"])
         d = sweep[dom]
         per_launch_ms = d["ms"] / d["launches"]
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+        if df64:
+            # FP32-pipe operations: 12 per real product term, 4 terms per complex
+            # multiply-add of 8 FP64-equivalent flops (normalisations not counted)
+            ops = d["flops"] * 6.0 / (d["ms"] * 1e-3) / 1e12
+            return {"kernel": dom, "bound": "alu", "achieved": round(ops, 3), "peak": round(FP32_PIPE_TOPS, 3),
+                    "unit": "Tops/s (FP32 pipe)", "frac": round(ops / FP32_PIPE_TOPS, 4), "traffic": None,
+                    "peak_source": "derived: 128 FP32 lanes x 152 SMs x 2.07 GHz",
+                    "fp64_equivalent_tflops": round(achieved, 4), "launch_ms": round(per_launch_ms, 4),
+                    "hbm_achieved_gbs": round(d["bytes"] / (d["ms"] * 1e-3) / 1e9, 1),
+                    "hbm_frac": round(d["bytes"] / (d["ms"] * 1e-3) / 1e9 / hbm, 4)}
         fam = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                    "share": round(v["ms"] / sum(x["ms"] for x in res["prof"].values()), 4),
                    "tflops": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 4),
@@ -335,6 +352,15 @@ def run_ours(args):
                           "columns_per_step": par["batch"], "e2e": par["e2e"], "roofline": roofline(par),
                           "gpu_launches": par["launches"], "clocks": par["clocks"],
                           "structure": "parity-conserving gates, parity-sector tiles (2^15 stored amplitudes)"}
+    if df_gen is not None:
+        line["df64"] = {"arith": "double-float (two floats per FP64 value, error-free transforms on the FP32 pipe)",
+                        "general": {"value": df_gen["value"], "unit": UNIT, "ms_per_step": df_gen["ms_per_step"],
+                                    "e2e": df_gen["e2e"], "roofline": roofline(df_gen, df64=True),
+                                    "gpu_launches": df_gen["launches"], "clocks": df_gen["clocks"]}}
+        if df_par is not None:
+            line["df64"]["parity"] = {"value": df_par["value"], "unit": UNIT, "ms_per_step": df_par["ms_per_step"],
+                                      "e2e": df_par["e2e"], "roofline": roofline(df_par, df64=True),
+                                      "gpu_launches": df_par["launches"], "clocks": df_par["clocks"]}
     if batched is not None:
         line["batched"] = batched
     if world == 1 and not args.no_cpu:
@@ -382,6 +408,7 @@ def main():
     ap.add_argument("--tile", type=int, default=0, help="columns per tile (power of two; 0 = automatic)")
     ap.add_argument("--general-only", action="store_true", help="skip the parity-gate measurement")
     ap.add_argument("--batched", action="store_true", help="also time 256 uneven problems batched vs plain")
+    ap.add_argument("--no-df64", action="store_true", help="skip the double-float arithmetic measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--sites", type=int, default=8, help="chain sites (n = 2 * sites); profiling cases only")
     ap.add_argument("--depth", type=int, default=11, help="brickwall layers; profiling cases only")

@@ -149,6 +149,21 @@ rq_status rq_set_columns(rq_ctx *ctx, int64_t col_begin, int64_t col_end);
  * workspace; RQ_ENOMEM if it does not fit. */
 rq_status rq_set_tile(rq_ctx *ctx, int columns_per_tile, int max_dirs);
 
+/* Arithmetic of the sweep kernels (forward, adjoint, environments).
+ * RQ_ARITH_FP64 (default): IEEE binary64 on the FP64 pipe.  RQ_ARITH_DF64:
+ * every amplitude and gate entry is kept as an unevaluated sum of two floats
+ * (about 48 significant bits) and the gate applications and gate-hole
+ * contractions run on the FP32 pipe with error-free transformations (two-sum,
+ * FMA two-product; a compensated dot product in twice the float precision),
+ * which GB300 executes far faster than FP64.  The target, the reductions and
+ * the Riemannian post-processing stay FP64; results agree with the FP64 ones
+ * to about 1e-13 relative (the tests hold both to 1e-12 against the FP64
+ * oracle).  The paper's kernels are FP64 on CPUs; this option has no
+ * counterpart there.  RQ_EINVAL for any other value. */
+#define RQ_ARITH_FP64 0
+#define RQ_ARITH_DF64 1
+rq_status rq_set_arithmetic(rq_ctx *ctx, int arith);
+
 /* Output space of rq_grad / rq_hvp (and their _dev variants).
  * RQ_SPACE_RIEMANNIAN (default): grad f = P_G(gbar) (Eq. grad_proj) and
  * Hess f(G)[X] (Eq. hessian_def) with X projected onto the tangent space.

@@ -71,6 +71,8 @@ struct rq_ctx {
     long long launches = 0;
     long long cols_cap = 0;
     int space = 0;  // 0 Riemannian outputs, 1 Euclidean (rq_set_gradient_space)
+    int arith = 0;  // 0 FP64 sweeps, 1 double-float sweeps (rq_set_arithmetic)
+    double2 *d_gates_df = nullptr, *d_dirs_df = nullptr;  // df64 copies (float4 per entry)
     // per-kernel profiling (events bracket every launch while enabled)
     struct ProfRec {
         int family;
@@ -181,6 +183,8 @@ void free_small(rq_ctx *ctx) {
     dev_free(ctx->d_in_gates);
     dev_free(ctx->d_dirs);
     dev_free(ctx->d_dirs_raw);
+    dev_free(ctx->d_gates_df);
+    dev_free(ctx->d_dirs_df);
     dev_free(ctx->d_param_of);
     dev_free(ctx->d_out);
     dev_free(ctx->d_cols);
@@ -314,11 +318,13 @@ rq_status ensure_small(rq_ctx *ctx, int k) {
         RQ_CUDA(cudaStreamSynchronize(ctx->stream));
         dev_free(ctx->d_dirs);
         dev_free(ctx->d_dirs_raw);
+        dev_free(ctx->d_dirs_df);
         dev_free(ctx->d_envd);
         dev_free(ctx->d_out);
         ctx->out_cap = 0;
         const int cap = std::max(k, 4);
         RQ_TRY(dev_alloc(ctx, &ctx->d_dirs, (long long)cap * ctx->P * 16, ctx->small_bytes));
+        RQ_TRY(dev_alloc(ctx, &ctx->d_dirs_df, (long long)cap * ctx->P * 16, ctx->small_bytes));
         RQ_TRY(dev_alloc(ctx, &ctx->d_dirs_raw, (long long)cap * ctx->P * 16, ctx->small_bytes));
         RQ_TRY(dev_alloc(ctx, &ctx->d_envd, (long long)cap * ctx->g * rq::kEnvDoubles, ctx->small_bytes));
         ctx->dirs_cap = ctx->envd_cap = cap;
@@ -497,10 +503,27 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
     }
     if (k > 0 && env_mode == 0) env_mode = 1;  // the HVP correction needs the gradient environments
     const bool want_env = env_mode == 1;
+    const bool df = ctx->arith == 1;
     if (env_mode != 2) RQ_CUDA(cudaMemsetAsync(ctx->d_env, 0, sizeof(double) * g * rq::kEnvDoubles, s));
     if (k > 0) RQ_CUDA(cudaMemsetAsync(ctx->d_envd, 0, sizeof(double) * (size_t)k * g * rq::kEnvDoubles, s));
     RQ_CUDA(cudaMemsetAsync(ctx->d_facc, 0, sizeof(double), s));
 
+    if (df) {  // df64 copies of the (masked) gates and (projected) directions
+        {
+            ProfScope ps(ctx, kFamGeometry, 0.0, 0.0);
+            rq::launch_to_df64(ctx->d_gates, ctx->d_gates_df, (long long)P * 16, s);
+        }
+        RQ_LAUNCHED();
+        if (k > 0) {
+            {
+                ProfScope ps(ctx, kFamGeometry, 0.0, 0.0);
+                rq::launch_to_df64(ctx->d_dirs, ctx->d_dirs_df, (long long)k * P * 16, s);
+            }
+            RQ_LAUNCHED();
+        }
+    }
+    const double2 *gsrc = df ? ctx->d_gates_df : ctx->d_gates;
+    const double2 *dsrc = df ? ctx->d_dirs_df : ctx->d_dirs;
     const int B = ctx->B;
     const long long tile = ctx->n_store * B;
     const long long set = tile * (g + 1);  // one checkpoint set
@@ -516,7 +539,8 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
             RQ_CUDA(cudaMemsetAsync(ctx->d_psi, 0, sizeof(double2) * tile, s));
             {
                 ProfScope ps(ctx, kFamInit, 0.0, (double)B * sizeof(double2));
-                rq::launch_init_unit(ctx->d_psi, cols, B, ctx->log2B, ctx->n_store, ctx->structure, s);
+                if (df) rq::launch_init_unit_df64(ctx->d_psi, cols, B, ctx->log2B, ctx->n_store, s);
+                else rq::launch_init_unit(ctx->d_psi, cols, B, ctx->log2B, ctx->n_store, ctx->structure, s);
             }
             RQ_LAUNCHED();
             for (int d = 0; d < kd; ++d) RQ_CUDA(cudaMemsetAsync(ctx->d_dpsi + d * set, 0, sizeof(double2) * tile, s));
@@ -530,8 +554,8 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                 a.dpsi_out = ctx->d_dpsi + (l + 1) * tile;
                 a.dir_stride = set;
                 a.kdirs = kd;
-                a.gate = ctx->d_gates + (long long)geo.param * 16;
-                a.dirs = ctx->d_dirs + ((long long)d0 * P + geo.param) * 16;
+                a.gate = gsrc + (long long)geo.param * 16;
+                a.dirs = dsrc + ((long long)d0 * P + geo.param) * 16;
                 a.xdir_stride = (long long)P * 16;
                 a.geo = geo;
                 a.log2B = ctx->log2B;
@@ -542,7 +566,8 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                     const double cm = geo.mode == rq::kGeneral ? 16.0 : (geo.mode == rq::kParity4 ? 8.0 : 4.0);
                     ProfScope ps(ctx, kFamFwd, (double)a.n_items * 8.0 * cm * (1 + 2 * kd),
                                  (double)a.n_items * amps * sizeof(double2) * 2 * (1 + kd));
-                    rq::launch_fwd(a, ctx->ncta, s);
+                    if (df) rq::launch_fwd_df64(a, ctx->ncta, s);
+                    else rq::launch_fwd(a, ctx->ncta, s);
                 }
                 RQ_LAUNCHED();
             }
@@ -550,8 +575,12 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
             RQ_CUDA(cudaMemsetAsync(ctx->d_lam, 0, sizeof(double2) * tile, s));
             {
                 ProfScope ps(ctx, kFamTarget, 0.0, 0.0);
-                rq::launch_scatter_target(target_dev(ctx), cols, B, ctx->log2B, ctx->structure, ctx->n, ctx->d_lam,
-                                          ctx->d_psi + g * tile, ctx->d_fpart, s);
+                if (df)
+                    rq::launch_scatter_target_df64(target_dev(ctx), cols, B, ctx->log2B, ctx->structure, ctx->n,
+                                                   ctx->d_lam, ctx->d_psi + g * tile, ctx->d_fpart, s);
+                else
+                    rq::launch_scatter_target(target_dev(ctx), cols, B, ctx->log2B, ctx->structure, ctx->n,
+                                              ctx->d_lam, ctx->d_psi + g * tile, ctx->d_fpart, s);
             }
             RQ_LAUNCHED();
             if (first) {
@@ -569,7 +598,7 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                 rq::BwdArgs a;
                 a.lam = ctx->d_lam;
                 a.psi = ctx->d_psi + l * tile;
-                a.gate = ctx->d_gates + (long long)geo.param * 16;
+                a.gate = gsrc + (long long)geo.param * 16;
                 a.geo = geo;
                 a.log2B = ctx->log2B;
                 a.tile_parity = par;
@@ -579,7 +608,7 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                     rq::BwdArgs b = a;
                     b.dlam = ctx->d_dlam + d * tile;
                     b.dpsi = ctx->d_dpsi + d * set + l * tile;
-                    b.dir = ctx->d_dirs + ((long long)(d0 + d) * P + geo.param) * 16;
+                    b.dir = dsrc + ((long long)(d0 + d) * P + geo.param) * 16;
                     b.accumulate = 1;
                     b.part = ctx->d_partd + ((long long)d * g + l) * ctx->ncta * rq::kEnvDoubles;
                     {
@@ -587,7 +616,8 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                         const double cm = geo.mode == rq::kGeneral ? 16.0 : (geo.mode == rq::kParity4 ? 8.0 : 4.0);
                         ProfScope ps(ctx, kFamBwdDir, (double)b.n_items * 8.0 * cm * (2 + 2 * b.update),
                                      (double)b.n_items * amps * sizeof(double2) * (4 + b.update));
-                        rq::launch_bwd_dir(b, ctx->ncta, s);
+                        if (df) rq::launch_bwd_dir_df64(b, ctx->ncta, s);
+                        else rq::launch_bwd_dir(b, ctx->ncta, s);
                     }
                     RQ_LAUNCHED();
                 }
@@ -602,7 +632,8 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                         const double cm = geo.mode == rq::kGeneral ? 16.0 : (geo.mode == rq::kParity4 ? 8.0 : 4.0);
                         ProfScope ps(ctx, kFamBwdBase, (double)a.n_items * 8.0 * cm * (a.accumulate + a.update),
                                      (double)a.n_items * amps * sizeof(double2) * (1 + a.accumulate + a.update));
-                        rq::launch_bwd_base(a, ctx->ncta, s);
+                        if (df) rq::launch_bwd_base_df64(a, ctx->ncta, s);
+                        else rq::launch_bwd_base(a, ctx->ncta, s);
                     }
                     RQ_LAUNCHED();
                 }
@@ -803,6 +834,7 @@ rq_status rq_setup_target(rq_ctx *ctx, const rq_target *tgt, const rq_circuit *c
     if (st == RQ_OK) st = dev_alloc(ctx, &ctx->d_facc, 1, ctx->small_bytes);
     if (st == RQ_OK) st = dev_alloc(ctx, &ctx->d_gates, (long long)P * 16, ctx->small_bytes);
     if (st == RQ_OK) st = dev_alloc(ctx, &ctx->d_in_gates, (long long)P * 16, ctx->small_bytes);
+    if (st == RQ_OK) st = dev_alloc(ctx, &ctx->d_gates_df, (long long)P * 16, ctx->small_bytes);
     if (st == RQ_OK) st = dev_alloc(ctx, &ctx->d_param_of, ctx->g, ctx->small_bytes);
     if (st == RQ_OK &&
         (cudaMemcpyAsync(ctx->d_param_of, ctx->param_of.data(), ctx->g * sizeof(int32_t), cudaMemcpyHostToDevice,
@@ -838,6 +870,14 @@ rq_status rq_set_tile(rq_ctx *ctx, int columns_per_tile, int max_dirs) {
     ctx->user_B = columns_per_tile;
     ctx->user_kc = max_dirs;
     return rebuild_tiles(ctx);
+}
+
+rq_status rq_set_arithmetic(rq_ctx *ctx, int arith) {
+    if (!ctx) return RQ_EINVAL;
+    if (arith != RQ_ARITH_FP64 && arith != RQ_ARITH_DF64)
+        return fail(ctx, RQ_EINVAL, "arithmetic %d is neither RQ_ARITH_FP64 nor RQ_ARITH_DF64", arith);
+    ctx->arith = arith;
+    return RQ_OK;
 }
 
 rq_status rq_set_gradient_space(rq_ctx *ctx, int space) {

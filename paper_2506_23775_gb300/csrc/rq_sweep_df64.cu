@@ -1,0 +1,555 @@
+// Double-float ("df64") variant of the sweep kernels.
+//
+// GB300 executes FP64 at 2 DFMA per clock per SM but FP32 at 128 FMA per
+// clock per SM.  These kernels keep every amplitude and gate entry as an
+// unevaluated sum of two floats, x = hi + lo with |lo| <= ulp(hi) / 2 (about
+// 48 significant bits), and run the gate applications and gate-hole
+// contractions of the sweep (same operations, same order of columns and
+// gates as the FP64 kernels in rq_sweep.cu) on the FP32 pipe:
+//
+//   * a product of two df64 numbers is hi*hi split exactly by an FMA
+//     (Dekker's two-product with a fused multiply-add) plus the two cross
+//     terms hi*lo + lo*hi; lo*lo (below 2^-48 relative) is dropped;
+//   * products are summed with Knuth's error-free two-sum on the high parts,
+//     the rounding errors and low parts collected in a float, and the result
+//     renormalised by one more two-sum (the compensated dot product of Ogita,
+//     Rump and Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput.
+//     26 (2005), in its twice-the-working-precision form).
+//
+// The storage of a complex amplitude is a float4 (re.hi, re.lo, im.hi,
+// im.lo): 16 bytes, like complex128, so tiles and checkpoints keep their
+// layout.  Environments are accumulated per thread in df64, converted to FP64
+// and reduced with the same fixed-order FP64 reductions as the FP64 path; the
+// target overlap, the reductions and the Riemannian post-processing stay FP64.
+// Every float operation below is an explicitly rounded intrinsic, so the
+// compiler can neither contract nor reassociate the error-free transforms.
+#include "rq_internal.h"
+
+namespace rq {
+namespace {
+
+struct Acc {
+    float h, l;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// a = x * y (first term of a sum)
+__device__ __forceinline__ void acc_set(Acc &a, float xh, float xl, float yh, float yl) {
+    a.h = __fmul_rn(xh, yh);
+    float e = __fmaf_rn(xh, yh, -a.h);
+    e = __fmaf_rn(xh, yl, e);
+    a.l = __fmaf_rn(xl, yh, e);
+}
+
+// a += x * y
+__device__ __forceinline__ void acc_mac(Acc &a, float xh, float xl, float yh, float yl) {
+    const float p = __fmul_rn(xh, yh);
+    float e = __fmaf_rn(xh, yh, -p);
+    e = __fmaf_rn(xh, yl, e);
+    e = __fmaf_rn(xl, yh, e);
+    float s, t;
+    two_sum(a.h, p, s, t);
+    a.h = s;
+    a.l = __fadd_rn(a.l, __fadd_rn(t, e));
+}
+
+struct CAcc {
+    Acc re, im;
+};
+
+__device__ __forceinline__ CAcc czero() { return CAcc{{0.f, 0.f}, {0.f, 0.f}}; }
+
+// c = g * x (complex, first term)
+__device__ __forceinline__ void cset(CAcc &c, const float4 g, const float4 x) {
+    acc_set(c.re, g.x, g.y, x.x, x.y);
+    acc_mac(c.re, -g.z, -g.w, x.z, x.w);
+    acc_set(c.im, g.x, g.y, x.z, x.w);
+    acc_mac(c.im, g.z, g.w, x.x, x.y);
+}
+
+// c += g * x
+__device__ __forceinline__ void cmac(CAcc &c, const float4 g, const float4 x) {
+    acc_mac(c.re, g.x, g.y, x.x, x.y);
+    acc_mac(c.re, -g.z, -g.w, x.z, x.w);
+    acc_mac(c.im, g.x, g.y, x.z, x.w);
+    acc_mac(c.im, g.z, g.w, x.x, x.y);
+}
+
+// c += conj(a) * b
+__device__ __forceinline__ void cmacc(CAcc &c, const float4 a, const float4 b) {
+    acc_mac(c.re, a.x, a.y, b.x, b.y);
+    acc_mac(c.re, a.z, a.w, b.z, b.w);
+    acc_mac(c.im, a.x, a.y, b.z, b.w);
+    acc_mac(c.im, -a.z, -a.w, b.x, b.y);
+}
+
+// c = conj(a) * b (first term)
+__device__ __forceinline__ void csetc(CAcc &c, const float4 a, const float4 b) {
+    acc_set(c.re, a.x, a.y, b.x, b.y);
+    acc_mac(c.re, a.z, a.w, b.z, b.w);
+    acc_set(c.im, a.x, a.y, b.z, b.w);
+    acc_mac(c.im, -a.z, -a.w, b.x, b.y);
+}
+
+__device__ __forceinline__ float4 fin(const CAcc &c) {
+    float4 r;
+    two_sum(c.re.h, c.re.l, r.x, r.y);
+    two_sum(c.im.h, c.im.l, r.z, r.w);
+    return r;
+}
+
+__device__ __forceinline__ double2 to_double(const CAcc &c) {
+    return make_double2((double)c.re.h + (double)c.re.l, (double)c.im.h + (double)c.im.l);
+}
+
+__device__ __forceinline__ long long insert_zero(long long r, int p) {
+    const long long lo = r & ((1LL << p) - 1);
+    return ((r >> p) << (p + 1)) | lo;
+}
+
+__device__ __forceinline__ void offsets4(long long r, long long b, int pa, int pb, int log2B, long long (&off)[4]) {
+    const int plo = pa < pb ? pa : pb;
+    const int phi = pa < pb ? pb : pa;
+    const long long x0 = insert_zero(insert_zero(r, plo), phi);
+    const long long sa = 1LL << pa, sb = 1LL << pb;
+    off[0] = (x0 << log2B) | b;
+    off[1] = ((x0 | sb) << log2B) | b;
+    off[2] = ((x0 | sa) << log2B) | b;
+    off[3] = ((x0 | sa | sb) << log2B) | b;
+}
+
+__device__ __forceinline__ void offsets2(long long r, long long b, int p, int qfirst, int parity, int log2B,
+                                         long long (&off)[2], int &i0, int &i1) {
+    const long long y0 = insert_zero(r, p);
+    off[0] = (y0 << log2B) | b;
+    off[1] = ((y0 | (1LL << p)) << log2B) | b;
+    const int e = (__popcll(y0) & 1) ^ parity;
+    if (e == 0) {
+        i0 = 0;
+        i1 = 3;
+    } else if (qfirst) {
+        i0 = 1;
+        i1 = 2;
+    } else {
+        i0 = 2;
+        i1 = 1;
+    }
+}
+
+// Local indices that a parity gate couples within its even block {0, 3} and
+// odd block {1, 2}: out[i] = sum over c in block(i).
+__device__ __forceinline__ int blk(int i, int u) {
+    // u = 0, 1: the two members of i's block
+    return (i == 0 || i == 3) ? (u == 0 ? 0 : 3) : (u == 0 ? 1 : 2);
+}
+
+__device__ __forceinline__ void block_reduce_store(const CAcc (&acc)[16], double *out) {
+    __shared__ double red[kThreads / 32][kEnvDoubles];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const double2 v = to_double(acc[i]);
+        double vx = v.x, vy = v.y;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            vx += __shfl_xor_sync(0xffffffffu, vx, o);
+            vy += __shfl_xor_sync(0xffffffffu, vy, o);
+        }
+        if (lane == 0) {
+            red[warp][2 * i] = vx;
+            red[warp][2 * i + 1] = vy;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kEnvDoubles) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) s += red[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------------- forward --
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) k_fwd_df(const FwdArgs a) {
+    __shared__ float4 sg[16];
+    __shared__ float4 sx[kMaxDirs][16];
+    const float4 *gate = reinterpret_cast<const float4 *>(a.gate);
+    const float4 *dirs = reinterpret_cast<const float4 *>(a.dirs);
+    if (threadIdx.x < 16) sg[threadIdx.x] = gate[threadIdx.x];
+    if (threadIdx.x < 16 * a.kdirs)
+        sx[threadIdx.x >> 4][threadIdx.x & 15] = dirs[(threadIdx.x >> 4) * a.xdir_stride + (threadIdx.x & 15)];
+    __syncthreads();
+    const float4 *psi_in = reinterpret_cast<const float4 *>(a.psi_in);
+    float4 *psi_out = reinterpret_cast<float4 *>(a.psi_out);
+    const float4 *dpsi_in = reinterpret_cast<const float4 *>(a.dpsi_in);
+    float4 *dpsi_out = reinterpret_cast<float4 *>(a.dpsi_out);
+    const long long Bm = (1LL << a.log2B) - 1;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.n_items; it += stride) {
+        const long long b = it & Bm, r = it >> a.log2B;
+        if (MODE == kGeneral || MODE == kParity4) {
+            long long off[4];
+            offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
+            float4 p[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) p[c] = __ldg(&psi_in[off[c]]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                CAcc q;
+                if (MODE == kGeneral) {
+                    cset(q, sg[i * 4 + 0], p[0]);
+#pragma unroll
+                    for (int c = 1; c < 4; ++c) cmac(q, sg[i * 4 + c], p[c]);
+                } else {
+                    cset(q, sg[i * 4 + blk(i, 0)], p[blk(i, 0)]);
+                    cmac(q, sg[i * 4 + blk(i, 1)], p[blk(i, 1)]);
+                }
+                psi_out[off[i]] = fin(q);
+            }
+            for (int d = 0; d < a.kdirs; ++d) {
+                const float4 *din = dpsi_in + d * a.dir_stride;
+                float4 *dout = dpsi_out + d * a.dir_stride;
+                float4 t[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) t[c] = __ldg(&din[off[c]]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    CAcc q;
+                    if (MODE == kGeneral) {
+                        cset(q, sg[i * 4 + 0], t[0]);
+#pragma unroll
+                        for (int c = 1; c < 4; ++c) cmac(q, sg[i * 4 + c], t[c]);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) cmac(q, sx[d][i * 4 + c], p[c]);
+                    } else {
+                        cset(q, sg[i * 4 + blk(i, 0)], t[blk(i, 0)]);
+                        cmac(q, sg[i * 4 + blk(i, 1)], t[blk(i, 1)]);
+                        cmac(q, sx[d][i * 4 + blk(i, 0)], p[blk(i, 0)]);
+                        cmac(q, sx[d][i * 4 + blk(i, 1)], p[blk(i, 1)]);
+                    }
+                    dout[off[i]] = fin(q);
+                }
+            }
+        } else {  // kParity2
+            long long off[2];
+            int i0, i1;
+            offsets2(r, b, a.geo.pa, a.geo.qfirst, a.tile_parity, a.log2B, off, i0, i1);
+            const float4 p0 = __ldg(&psi_in[off[0]]), p1 = __ldg(&psi_in[off[1]]);
+            CAcc q0, q1;
+            cset(q0, sg[i0 * 4 + i0], p0);
+            cmac(q0, sg[i0 * 4 + i1], p1);
+            cset(q1, sg[i1 * 4 + i0], p0);
+            cmac(q1, sg[i1 * 4 + i1], p1);
+            psi_out[off[0]] = fin(q0);
+            psi_out[off[1]] = fin(q1);
+            for (int d = 0; d < a.kdirs; ++d) {
+                const float4 *din = dpsi_in + d * a.dir_stride;
+                float4 *dout = dpsi_out + d * a.dir_stride;
+                const float4 t0 = __ldg(&din[off[0]]), t1 = __ldg(&din[off[1]]);
+                cset(q0, sg[i0 * 4 + i0], t0);
+                cmac(q0, sg[i0 * 4 + i1], t1);
+                cmac(q0, sx[d][i0 * 4 + i0], p0);
+                cmac(q0, sx[d][i0 * 4 + i1], p1);
+                cset(q1, sg[i1 * 4 + i0], t0);
+                cmac(q1, sg[i1 * 4 + i1], t1);
+                cmac(q1, sx[d][i1 * 4 + i0], p0);
+                cmac(q1, sx[d][i1 * 4 + i1], p1);
+                dout[off[0]] = fin(q0);
+                dout[off[1]] = fin(q1);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------- backward base --
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) k_bwd_base_df(const BwdArgs a) {
+    __shared__ float4 sg[16];
+    const float4 *gate = reinterpret_cast<const float4 *>(a.gate);
+    if (threadIdx.x < 16) sg[threadIdx.x] = gate[threadIdx.x];
+    __syncthreads();
+    float4 *lam = reinterpret_cast<float4 *>(a.lam);
+    const float4 *psi = reinterpret_cast<const float4 *>(a.psi);
+    const int accumulate = a.accumulate;
+    CAcc E[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) E[i] = czero();
+    const long long Bm = (1LL << a.log2B) - 1;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.n_items; it += stride) {
+        const long long b = it & Bm, r = it >> a.log2B;
+        if (MODE == kGeneral || MODE == kParity4) {
+            long long off[4];
+            offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
+            float4 l[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) l[c] = lam[off[c]];
+            if (accumulate) {
+                float4 p[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) p[c] = __ldg(&psi[off[c]]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (MODE == kGeneral) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) cmacc(E[i * 4 + c], l[i], p[c]);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) cmacc(E[i * 4 + blk(i, u)], l[i], p[blk(i, u)]);
+                    }
+                }
+            }
+            if (a.update) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    CAcc q;
+                    if (MODE == kGeneral) {
+                        csetc(q, sg[0 * 4 + i], l[0]);
+#pragma unroll
+                        for (int c = 1; c < 4; ++c) cmacc(q, sg[c * 4 + i], l[c]);
+                    } else {
+                        csetc(q, sg[blk(i, 0) * 4 + i], l[blk(i, 0)]);
+                        cmacc(q, sg[blk(i, 1) * 4 + i], l[blk(i, 1)]);
+                    }
+                    lam[off[i]] = fin(q);
+                }
+            }
+        } else {  // kParity2
+            long long off[2];
+            int i0, i1;
+            offsets2(r, b, a.geo.pa, a.geo.qfirst, a.tile_parity, a.log2B, off, i0, i1);
+            const float4 l0 = lam[off[0]], l1 = lam[off[1]];
+            if (accumulate) {
+                const float4 p0 = __ldg(&psi[off[0]]), p1 = __ldg(&psi[off[1]]);
+                // E[i0][i0], E[i0][i1], E[i1][i0], E[i1][i1], static indices per block
+                if (i0 == 0) {
+                    cmacc(E[0], l0, p0); cmacc(E[3], l0, p1); cmacc(E[12], l1, p0); cmacc(E[15], l1, p1);
+                } else if (i0 == 1) {
+                    cmacc(E[5], l0, p0); cmacc(E[6], l0, p1); cmacc(E[9], l1, p0); cmacc(E[10], l1, p1);
+                } else {
+                    cmacc(E[10], l0, p0); cmacc(E[9], l0, p1); cmacc(E[6], l1, p0); cmacc(E[5], l1, p1);
+                }
+            }
+            if (a.update) {
+                CAcc q0, q1;
+                csetc(q0, sg[i0 * 4 + i0], l0);
+                cmacc(q0, sg[i1 * 4 + i0], l1);
+                csetc(q1, sg[i0 * 4 + i1], l0);
+                cmacc(q1, sg[i1 * 4 + i1], l1);
+                lam[off[0]] = fin(q0);
+                lam[off[1]] = fin(q1);
+            }
+        }
+    }
+    if (accumulate) block_reduce_store(E, a.part + (long long)blockIdx.x * kEnvDoubles);
+}
+
+// ----------------------------------------------------- backward direction --
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) k_bwd_dir_df(const BwdArgs a) {
+    __shared__ float4 sg[16];
+    __shared__ float4 sx[16];
+    const float4 *gate = reinterpret_cast<const float4 *>(a.gate);
+    const float4 *dir = reinterpret_cast<const float4 *>(a.dir);
+    if (threadIdx.x < 16) {
+        sg[threadIdx.x] = gate[threadIdx.x];
+        sx[threadIdx.x] = dir[threadIdx.x];
+    }
+    __syncthreads();
+    const float4 *lam = reinterpret_cast<const float4 *>(a.lam);
+    float4 *dlam = reinterpret_cast<float4 *>(a.dlam);
+    const float4 *psi = reinterpret_cast<const float4 *>(a.psi);
+    const float4 *dpsi = reinterpret_cast<const float4 *>(a.dpsi);
+    CAcc E[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) E[i] = czero();
+    const long long Bm = (1LL << a.log2B) - 1;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.n_items; it += stride) {
+        const long long b = it & Bm, r = it >> a.log2B;
+        if (MODE == kGeneral || MODE == kParity4) {
+            long long off[4];
+            offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
+            float4 l[4], dl[4], p[4], dp[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                l[c] = __ldg(&lam[off[c]]);
+                dl[c] = dlam[off[c]];
+                p[c] = __ldg(&psi[off[c]]);
+                dp[c] = __ldg(&dpsi[off[c]]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (MODE == kGeneral) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        cmacc(E[i * 4 + c], dl[i], p[c]);
+                        cmacc(E[i * 4 + c], l[i], dp[c]);
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        cmacc(E[i * 4 + blk(i, u)], dl[i], p[blk(i, u)]);
+                        cmacc(E[i * 4 + blk(i, u)], l[i], dp[blk(i, u)]);
+                    }
+                }
+            }
+            if (a.update) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    CAcc q;
+                    if (MODE == kGeneral) {
+                        csetc(q, sg[0 * 4 + i], dl[0]);
+#pragma unroll
+                        for (int c = 1; c < 4; ++c) cmacc(q, sg[c * 4 + i], dl[c]);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) cmacc(q, sx[c * 4 + i], l[c]);
+                    } else {
+                        csetc(q, sg[blk(i, 0) * 4 + i], dl[blk(i, 0)]);
+                        cmacc(q, sg[blk(i, 1) * 4 + i], dl[blk(i, 1)]);
+                        cmacc(q, sx[blk(i, 0) * 4 + i], l[blk(i, 0)]);
+                        cmacc(q, sx[blk(i, 1) * 4 + i], l[blk(i, 1)]);
+                    }
+                    dlam[off[i]] = fin(q);
+                }
+            }
+        } else {  // kParity2
+            long long off[2];
+            int i0, i1;
+            offsets2(r, b, a.geo.pa, a.geo.qfirst, a.tile_parity, a.log2B, off, i0, i1);
+            const float4 l0 = __ldg(&lam[off[0]]), l1 = __ldg(&lam[off[1]]);
+            const float4 d0 = dlam[off[0]], d1 = dlam[off[1]];
+            const float4 p0 = __ldg(&psi[off[0]]), p1 = __ldg(&psi[off[1]]);
+            const float4 t0 = __ldg(&dpsi[off[0]]), t1 = __ldg(&dpsi[off[1]]);
+            if (i0 == 0) {
+                cmacc(E[0], d0, p0); cmacc(E[0], l0, t0); cmacc(E[3], d0, p1); cmacc(E[3], l0, t1);
+                cmacc(E[12], d1, p0); cmacc(E[12], l1, t0); cmacc(E[15], d1, p1); cmacc(E[15], l1, t1);
+            } else if (i0 == 1) {
+                cmacc(E[5], d0, p0); cmacc(E[5], l0, t0); cmacc(E[6], d0, p1); cmacc(E[6], l0, t1);
+                cmacc(E[9], d1, p0); cmacc(E[9], l1, t0); cmacc(E[10], d1, p1); cmacc(E[10], l1, t1);
+            } else {
+                cmacc(E[10], d0, p0); cmacc(E[10], l0, t0); cmacc(E[9], d0, p1); cmacc(E[9], l0, t1);
+                cmacc(E[6], d1, p0); cmacc(E[6], l1, t0); cmacc(E[5], d1, p1); cmacc(E[5], l1, t1);
+            }
+            if (a.update) {
+                CAcc q0, q1;
+                csetc(q0, sg[i0 * 4 + i0], d0);
+                cmacc(q0, sg[i1 * 4 + i0], d1);
+                cmacc(q0, sx[i0 * 4 + i0], l0);
+                cmacc(q0, sx[i1 * 4 + i0], l1);
+                csetc(q1, sg[i0 * 4 + i1], d0);
+                cmacc(q1, sg[i1 * 4 + i1], d1);
+                cmacc(q1, sx[i0 * 4 + i1], l0);
+                cmacc(q1, sx[i1 * 4 + i1], l1);
+                dlam[off[0]] = fin(q0);
+                dlam[off[1]] = fin(q1);
+            }
+        }
+    }
+    block_reduce_store(E, a.part + (long long)blockIdx.x * kEnvDoubles);
+}
+
+// psi_0 = |j_b> (the tile is zeroed before): df64 one = (1, 0, 0, 0).
+__global__ void k_init_unit_df(float4 *psi0, const int32_t *cols, int B, int log2B, long long mask) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const int j = cols[b];
+    if (j < 0) return;
+    psi0[(((long long)j & mask) << log2B) | b] = make_float4(1.f, 0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ float4 split(double2 v) {
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    return make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
+}
+
+// complex128 -> df64 for gates and directions
+__global__ void k_to_df64(const double2 *in, float4 *out, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = split(in[i]);
+}
+
+// lambda_g = U|j_b> in df64 and the cost summands in FP64 (see rq_target.cu).
+__global__ void k_scatter_target_df(const TargetDev t, const int32_t *cols, int log2B, long long mask,
+                                    float4 *lam, const float4 *psi, double *fpart) {
+    const int b = blockIdx.x;
+    const int j = cols[b];
+    double acc = 0.0;
+    if (j >= 0) {
+        const int s = t.sec_of[j];
+        const long long m = t.off_basis[s + 1] - t.off_basis[s];
+        const double2 *ucol = t.U + t.off_u[s] + (long long)t.pos[j] * m;
+        const int32_t *bas = t.basis + t.off_basis[s];
+        for (long long r = threadIdx.x; r < m; r += blockDim.x) {
+            const long long o = (((long long)bas[r] & mask) << log2B) | b;
+            const double2 u = ucol[r];
+            const float4 p = psi[o];
+            lam[o] = split(u);
+            acc = fma(u.x, (double)p.x + (double)p.y, acc);
+            acc = fma(u.y, (double)p.z + (double)p.w, acc);
+        }
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+        fpart[b] = -sum;
+    }
+}
+
+}  // namespace
+
+void launch_fwd_df64(const FwdArgs &a, int grid, cudaStream_t s) {
+    switch (a.geo.mode) {
+        case kGeneral: k_fwd_df<kGeneral><<<grid, kThreads, 0, s>>>(a); break;
+        case kParity4: k_fwd_df<kParity4><<<grid, kThreads, 0, s>>>(a); break;
+        default: k_fwd_df<kParity2><<<grid, kThreads, 0, s>>>(a); break;
+    }
+}
+
+void launch_bwd_base_df64(const BwdArgs &a, int grid, cudaStream_t s) {
+    switch (a.geo.mode) {
+        case kGeneral: k_bwd_base_df<kGeneral><<<grid, kThreads, 0, s>>>(a); break;
+        case kParity4: k_bwd_base_df<kParity4><<<grid, kThreads, 0, s>>>(a); break;
+        default: k_bwd_base_df<kParity2><<<grid, kThreads, 0, s>>>(a); break;
+    }
+}
+
+void launch_bwd_dir_df64(const BwdArgs &a, int grid, cudaStream_t s) {
+    switch (a.geo.mode) {
+        case kGeneral: k_bwd_dir_df<kGeneral><<<grid, kThreads, 0, s>>>(a); break;
+        case kParity4: k_bwd_dir_df<kParity4><<<grid, kThreads, 0, s>>>(a); break;
+        default: k_bwd_dir_df<kParity2><<<grid, kThreads, 0, s>>>(a); break;
+    }
+}
+
+void launch_init_unit_df64(double2 *psi0, const int32_t *cols, int B, int log2B, long long n_store,
+                           cudaStream_t s) {
+    k_init_unit_df<<<(B + 127) / 128, 128, 0, s>>>(reinterpret_cast<float4 *>(psi0), cols, B, log2B, n_store - 1);
+}
+
+void launch_to_df64(const double2 *in, double2 *out, long long n, cudaStream_t s) {
+    if (n <= 0) return;
+    k_to_df64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, reinterpret_cast<float4 *>(out), n);
+}
+
+void launch_scatter_target_df64(const TargetDev &t, const int32_t *cols, int B, int log2B, int parity_layout,
+                                int n, double2 *lam, const double2 *psi_final, double *fpart, cudaStream_t s) {
+    const long long mask = parity_layout ? ((1LL << (n - 1)) - 1) : ((1LL << n) - 1);
+    k_scatter_target_df<<<B, 128, 0, s>>>(t, cols, log2B, mask, reinterpret_cast<float4 *>(lam),
+                                          reinterpret_cast<const float4 *>(psi_final), fpart);
+}
+
+}  // namespace rq

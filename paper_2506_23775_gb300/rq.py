@@ -24,7 +24,7 @@ EXPORTS = ("rq_create", "rq_destroy", "rq_setup_target", "rq_set_columns", "rq_s
            "rq_tr_step", "rq_target_column", "rq_get_info", "rq_profile_start", "rq_profile_stop",
            "rq_cost_static", "rq_set_gradient_space", "rq_batch_create", "rq_batch_destroy",
            "rq_batch_add", "rq_batch_set_tile", "rq_batch_hvp", "rq_batch_info", "rq_batch_last_error",
-           "rq_last_error")
+           "rq_set_arithmetic", "rq_last_error")
 
 
 class RQCircuit(C.Structure):
@@ -93,6 +93,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "rq_profile_start": ([vp], C.c_int),
         "rq_cost_static": ([vp, dp, dp], C.c_int),
         "rq_set_gradient_space": ([vp, C.c_int], C.c_int),
+        "rq_set_arithmetic": ([vp, C.c_int], C.c_int),
         "rq_batch_create": ([C.POINTER(vp), C.c_int], C.c_int),
         "rq_batch_destroy": ([vp], C.c_int),
         "rq_batch_add": ([vp, C.POINTER(RQTarget), C.POINTER(RQCircuit), C.POINTER(C.c_int)], C.c_int),
@@ -187,6 +188,10 @@ class Context:
         """0: Riemannian outputs (default); 1: Euclidean gradient and Hessian."""
         self._check(self._lib.rq_set_gradient_space(self._h, int(space)))
         self._space = int(space)
+
+    def set_arithmetic(self, arith: int):
+        """0: FP64 sweeps (default); 1: double-float sweeps on the FP32 pipe."""
+        self._check(self._lib.rq_set_arithmetic(self._h, int(arith)))
 
     def stream_handle(self):
         """The cudaStream_t given at creation (None: a library-owned stream)."""
