@@ -149,6 +149,21 @@ rq_status rq_set_columns(rq_ctx *ctx, int64_t col_begin, int64_t col_end);
  * workspace; RQ_ENOMEM if it does not fit. */
 rq_status rq_set_tile(rq_ctx *ctx, int columns_per_tile, int max_dirs);
 
+/* Translation-representative basis sums (paper Sec. "Exploiting
+ * translational invariance", applied here to the basis sum).  If the chain is
+ * periodic and the circuit is invariant under shifting every site by
+ * shift_sites (checked: in each run of pairwise disjoint gates the set of
+ * (qubit pair, parameter) maps onto itself, e.g. one tied gate per brickwall
+ * layer with shift_sites = 2), U and C(G) both commute with the shift T, so the
+ * summand of Eq. f_target_sum_unit_vec -- and the tied gradient and HVP
+ * summands -- are equal on every orbit {j, Tj, T^2 j, ...}.  The sums then run
+ * over one representative per orbit weighted by the orbit size (about L /
+ * shift_sites times fewer columns).  Requires the whole basis as the column
+ * range; shift_sites = 0 switches back to plain sums.  RQ_EINVAL if the chain
+ * is open, the shift does not divide the sites, or the circuit is not
+ * invariant. */
+rq_status rq_set_translation(rq_ctx *ctx, int shift_sites);
+
 /* Arithmetic of the sweep kernels (forward, adjoint, environments).
  * RQ_ARITH_FP64 (default): IEEE binary64 on the FP64 pipe.  RQ_ARITH_DF64:
  * every amplitude and gate entry is kept as an unevaluated sum of two floats

@@ -72,6 +72,11 @@ struct rq_ctx {
     long long cols_cap = 0;
     int space = 0;  // 0 Riemannian outputs, 1 Euclidean (rq_set_gradient_space)
     int arith = 0;  // 0 FP64 sweeps, 1 double-float sweeps (rq_set_arithmetic)
+    // translation-representative basis sums (rq_set_translation)
+    int tshift = 0;
+    std::vector<int32_t> reps;     // orbit representatives, ascending
+    std::vector<double> rep_w;     // orbit sizes
+    double *d_wts = nullptr;       // per tile column, parallel to d_cols
     double2 *d_gates_df = nullptr, *d_dirs_df = nullptr;  // df64 copies (float4 per entry)
     // per-kernel profiling (events bracket every launch while enabled)
     struct ProfRec {
@@ -188,6 +193,7 @@ void free_small(rq_ctx *ctx) {
     dev_free(ctx->d_param_of);
     dev_free(ctx->d_out);
     dev_free(ctx->d_cols);
+    dev_free(ctx->d_wts);
     ctx->cols_cap = 0;
     ctx->envd_cap = ctx->dirs_cap = 0;
     ctx->out_cap = 0;
@@ -216,9 +222,23 @@ int ilog2(long long v) {
 
 // Column lists of the current range: one list (general gates) or the even-
 // then the odd-parity columns (parity gates: every tile shares one parity).
-void column_groups(const rq_ctx *ctx, std::vector<std::vector<int32_t>> &groups, std::vector<int> &parity) {
+void column_groups(const rq_ctx *ctx, std::vector<std::vector<int32_t>> &groups, std::vector<int> &parity,
+                   std::vector<std::vector<double>> *weights = nullptr) {
     groups.clear();
     parity.clear();
+    if (weights) weights->clear();
+    if (ctx->tshift > 0) {  // weighted orbit representatives (the range is the whole basis)
+        const int ng = ctx->structure == 1 ? 2 : 1;
+        groups.resize(ng);
+        if (weights) weights->resize(ng);
+        for (int gi = 0; gi < ng; ++gi) parity.push_back(gi);
+        for (size_t i = 0; i < ctx->reps.size(); ++i) {
+            const int gi = ctx->structure == 1 ? (__builtin_popcountll(ctx->reps[i]) & 1) : 0;
+            groups[gi].push_back(ctx->reps[i]);
+            if (weights) (*weights)[gi].push_back(ctx->rep_w[i]);
+        }
+        return;
+    }
     if (ctx->structure == 1) {
         std::vector<int32_t> ev, od;
         for (long long j = ctx->c0; j < ctx->c1; ++j) (__builtin_popcountll(j) & 1 ? od : ev).push_back((int32_t)j);
@@ -245,8 +265,9 @@ long long bytes_per_column(const rq_ctx *ctx, int kc) {
 rq_status rebuild_tiles(rq_ctx *ctx) {
     RQ_CUDA(cudaStreamSynchronize(ctx->stream));
     std::vector<std::vector<int32_t>> groups;
+    std::vector<std::vector<double>> gw;
     std::vector<int> gpar;
-    column_groups(ctx, groups, gpar);
+    column_groups(ctx, groups, gpar, &gw);
     long long largest = 1;
     for (auto &gr : groups) largest = std::max<long long>(largest, (long long)gr.size());
     const int bcap = ctx->user_B > 0 ? ctx->user_B : (int)std::min<long long>(512, 1LL << ilog2(largest));
@@ -273,11 +294,16 @@ rq_status rebuild_tiles(rq_ctx *ctx) {
     const long long items = std::max<long long>(1, ctx->n_store / 4 * B);
     const int ncta = (int)std::min<long long>((long long)ctx->sms * rq::kCtasPerSm, (items + rq::kThreads - 1) / rq::kThreads);
     std::vector<int32_t> cols;
+    std::vector<double> wts;
     std::vector<int> tpar;
+    const bool weighted = ctx->tshift > 0;
     for (size_t gi = 0; gi < groups.size(); ++gi) {
         const auto &gr = groups[gi];
         for (size_t s = 0; s < gr.size(); s += B) {
-            for (int b = 0; b < B; ++b) cols.push_back(s + b < gr.size() ? gr[s + b] : -1);
+            for (int b = 0; b < B; ++b) {
+                cols.push_back(s + b < gr.size() ? gr[s + b] : -1);
+                if (weighted) wts.push_back(s + b < gr.size() ? gw[gi][s + b] : 0.0);
+            }
             tpar.push_back(gpar[gi]);
         }
     }
@@ -299,8 +325,10 @@ rq_status rebuild_tiles(rq_ctx *ctx) {
     }
     if ((long long)cols.size() > ctx->cols_cap) {
         dev_free(ctx->d_cols);
+        dev_free(ctx->d_wts);
         ctx->cols_cap = 0;
         RQ_TRY(dev_alloc(ctx, &ctx->d_cols, (long long)cols.size(), ctx->small_bytes));
+        RQ_TRY(dev_alloc(ctx, &ctx->d_wts, (long long)cols.size(), ctx->small_bytes));
         ctx->cols_cap = (long long)cols.size();
     }
     ctx->tile_parity = tpar;
@@ -308,6 +336,9 @@ rq_status rebuild_tiles(rq_ctx *ctx) {
     if (!cols.empty()) {
         RQ_CUDA(cudaMemcpyAsync(ctx->d_cols, cols.data(), cols.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                                 ctx->stream));
+        if (weighted)
+            RQ_CUDA(cudaMemcpyAsync(ctx->d_wts, wts.data(), wts.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                    ctx->stream));
         RQ_CUDA(cudaStreamSynchronize(ctx->stream));
     }
     return RQ_OK;
@@ -535,6 +566,7 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
         const bool first = ch == 0;
         for (int ti = 0; ti < ctx->n_tiles; ++ti) {
             const int32_t *cols = ctx->d_cols + (long long)ti * B;
+            const double *wts = ctx->tshift > 0 ? ctx->d_wts + (long long)ti * B : nullptr;
             const int par = ctx->tile_parity[ti];
             RQ_CUDA(cudaMemsetAsync(ctx->d_psi, 0, sizeof(double2) * tile, s));
             {
@@ -576,10 +608,10 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
             {
                 ProfScope ps(ctx, kFamTarget, 0.0, 0.0);
                 if (df)
-                    rq::launch_scatter_target_df64(target_dev(ctx), cols, B, ctx->log2B, ctx->structure, ctx->n,
+                    rq::launch_scatter_target_df64(target_dev(ctx), cols, wts, B, ctx->log2B, ctx->structure, ctx->n,
                                                    ctx->d_lam, ctx->d_psi + g * tile, ctx->d_fpart, s);
                 else
-                    rq::launch_scatter_target(target_dev(ctx), cols, B, ctx->log2B, ctx->structure, ctx->n,
+                    rq::launch_scatter_target(target_dev(ctx), cols, wts, B, ctx->log2B, ctx->structure, ctx->n,
                                               ctx->d_lam, ctx->d_psi + g * tile, ctx->d_fpart, s);
             }
             RQ_LAUNCHED();
@@ -843,6 +875,9 @@ rq_status rq_setup_target(rq_ctx *ctx, const rq_target *tgt, const rq_circuit *c
         st = fail(ctx, RQ_ECUDA, "copy of param_of failed");
     ctx->c0 = 0;
     ctx->c1 = 1LL << ctx->n;
+    ctx->tshift = 0;
+    ctx->reps.clear();
+    ctx->rep_w.clear();
     ctx->ready = true;
     if (st == RQ_OK) st = ensure_small(ctx, 1);
     if (st == RQ_OK) st = rebuild_tiles(ctx);
@@ -856,6 +891,8 @@ rq_status rq_set_columns(rq_ctx *ctx, int64_t col_begin, int64_t col_end) {
     if (col_begin < 0 || col_end < col_begin || col_end > (1LL << ctx->n))
         return fail(ctx, RQ_EINVAL, "column range [%lld, %lld) outside [0, %lld)", (long long)col_begin,
                     (long long)col_end, 1LL << ctx->n);
+    if (ctx->tshift > 0 && (col_begin != 0 || col_end != (1LL << ctx->n)))
+        return fail(ctx, RQ_EINVAL, "translation-representative sums cover the whole basis; disable them first");
     ctx->c0 = col_begin;
     ctx->c1 = col_end;
     return rebuild_tiles(ctx);
@@ -869,6 +906,71 @@ rq_status rq_set_tile(rq_ctx *ctx, int columns_per_tile, int max_dirs) {
     if (max_dirs < 0 || max_dirs > rq::kMaxDirs) return fail(ctx, RQ_EINVAL, "max_dirs %d outside [0, %d]", max_dirs, rq::kMaxDirs);
     ctx->user_B = columns_per_tile;
     ctx->user_kc = max_dirs;
+    return rebuild_tiles(ctx);
+}
+
+rq_status rq_set_translation(rq_ctx *ctx, int shift_sites) {
+    if (!ctx) return RQ_EINVAL;
+    if (!ctx->ready) return fail(ctx, RQ_ESTATE, "no target set up");
+    const int L = ctx->L, n = ctx->n;
+    if (shift_sites == 0) {
+        ctx->tshift = 0;
+        ctx->reps.clear();
+        ctx->rep_w.clear();
+        return rebuild_tiles(ctx);
+    }
+    if (shift_sites < 0 || shift_sites >= L || L % shift_sites != 0)
+        return fail(ctx, RQ_EINVAL, "shift %d must divide the %d sites and be smaller", shift_sites, L);
+    if (!ctx->tgt.periodic) return fail(ctx, RQ_EINVAL, "translation symmetry needs a periodic chain");
+    // qubit map of the shift: site j -> j + s (mod L) on both spin chains
+    std::vector<int> qmap(n);
+    for (int q = 0; q < n; ++q) qmap[q] = (q < L) ? (q + shift_sites) % L : L + (q - L + shift_sites) % L;
+    // the circuit must be invariant: in every maximal run of pairwise disjoint
+    // (hence commuting) gates, the set of (pair, parameter) maps onto itself
+    size_t l0 = 0;
+    while (l0 < (size_t)ctx->g) {
+        size_t l1 = l0;
+        unsigned long long used = 0;
+        while (l1 < (size_t)ctx->g) {
+            const unsigned long long m = (1ULL << ctx->pairs[2 * l1]) | (1ULL << ctx->pairs[2 * l1 + 1]);
+            if (used & m) break;
+            used |= m;
+            ++l1;
+        }
+        for (size_t l = l0; l < l1; ++l) {
+            const int a = qmap[ctx->pairs[2 * l]], b = qmap[ctx->pairs[2 * l + 1]];
+            bool found = false;
+            for (size_t m2 = l0; m2 < l1 && !found; ++m2)
+                found = ctx->pairs[2 * m2] == a && ctx->pairs[2 * m2 + 1] == b && ctx->param_of[m2] == ctx->param_of[l];
+            if (!found)
+                return fail(ctx, RQ_EINVAL, "gate %zu on (%d, %d) has no shifted copy in its layer: the circuit is "
+                            "not invariant under a shift by %d sites", l, ctx->pairs[2 * l], ctx->pairs[2 * l + 1],
+                            shift_sites);
+        }
+        l0 = l1;
+    }
+    if (ctx->c0 != 0 || ctx->c1 != (1LL << n))
+        return fail(ctx, RQ_EINVAL, "translation-representative sums need the whole basis as the column range");
+    // orbits of the basis under the shift: smallest member represents, weight = orbit size
+    const long long dim = 1LL << n;
+    std::vector<char> seen(dim, 0);
+    ctx->reps.clear();
+    ctx->rep_w.clear();
+    for (long long x = 0; x < dim; ++x) {
+        if (seen[x]) continue;
+        long long y = x, size = 0;
+        do {
+            seen[y] = 1;
+            ++size;
+            long long z = 0;
+            for (int q = 0; q < n; ++q)
+                if ((y >> (n - 1 - q)) & 1) z |= 1LL << (n - 1 - qmap[q]);
+            y = z;
+        } while (y != x);
+        ctx->reps.push_back((int32_t)x);
+        ctx->rep_w.push_back((double)size);
+    }
+    ctx->tshift = shift_sites;
     return rebuild_tiles(ctx);
 }
 

@@ -89,11 +89,12 @@ void launch_bwd_base_df64(const BwdArgs &a, int grid, cudaStream_t s);
 void launch_bwd_dir_df64(const BwdArgs &a, int grid, cudaStream_t s);
 void launch_init_unit_df64(double2 *psi0, const int32_t *cols, int B, int log2B, long long n_store, cudaStream_t s);
 void launch_to_df64(const double2 *in, double2 *out, long long n, cudaStream_t s);
-void launch_scatter_target_df64(const TargetDev &t, const int32_t *cols, int B, int log2B, int parity_layout,
-                                int n, double2 *lam, const double2 *psi_final, double *fpart, cudaStream_t s);
+void launch_scatter_target_df64(const TargetDev &t, const int32_t *cols, const double *wts, int B, int log2B,
+                                int parity_layout, int n, double2 *lam, const double2 *psi_final, double *fpart,
+                                cudaStream_t s);
 
 // Launchers (rq_target.cu).
-void launch_scatter_target(const TargetDev &t, const int32_t *cols, int B, int log2B,
+void launch_scatter_target(const TargetDev &t, const int32_t *cols, const double *wts, int B, int log2B,
                            int parity_layout, int n, double2 *lam, const double2 *psi_final,
                            double *fpart, cudaStream_t s);
 void launch_cheb_step(const TargetDev &t, int n_sectors, long long total, const double *cur,

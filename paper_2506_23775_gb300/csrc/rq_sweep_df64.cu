@@ -479,10 +479,11 @@ __global__ void k_to_df64(const double2 *in, float4 *out, long long n) {
 }
 
 // lambda_g = U|j_b> in df64 and the cost summands in FP64 (see rq_target.cu).
-__global__ void k_scatter_target_df(const TargetDev t, const int32_t *cols, int log2B, long long mask,
-                                    float4 *lam, const float4 *psi, double *fpart) {
+__global__ void k_scatter_target_df(const TargetDev t, const int32_t *cols, const double *wts, int log2B,
+                                    long long mask, float4 *lam, const float4 *psi, double *fpart) {
     const int b = blockIdx.x;
     const int j = cols[b];
+    const double wb = wts ? wts[b] : 1.0;
     double acc = 0.0;
     if (j >= 0) {
         const int s = t.sec_of[j];
@@ -491,7 +492,7 @@ __global__ void k_scatter_target_df(const TargetDev t, const int32_t *cols, int 
         const int32_t *bas = t.basis + t.off_basis[s];
         for (long long r = threadIdx.x; r < m; r += blockDim.x) {
             const long long o = (((long long)bas[r] & mask) << log2B) | b;
-            const double2 u = ucol[r];
+            const double2 u = make_double2(wb * ucol[r].x, wb * ucol[r].y);
             const float4 p = psi[o];
             lam[o] = split(u);
             acc = fma(u.x, (double)p.x + (double)p.y, acc);
@@ -545,10 +546,11 @@ void launch_to_df64(const double2 *in, double2 *out, long long n, cudaStream_t s
     k_to_df64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, reinterpret_cast<float4 *>(out), n);
 }
 
-void launch_scatter_target_df64(const TargetDev &t, const int32_t *cols, int B, int log2B, int parity_layout,
-                                int n, double2 *lam, const double2 *psi_final, double *fpart, cudaStream_t s) {
+void launch_scatter_target_df64(const TargetDev &t, const int32_t *cols, const double *wts, int B, int log2B,
+                                int parity_layout, int n, double2 *lam, const double2 *psi_final, double *fpart,
+                                cudaStream_t s) {
     const long long mask = parity_layout ? ((1LL << (n - 1)) - 1) : ((1LL << n) - 1);
-    k_scatter_target_df<<<B, 128, 0, s>>>(t, cols, log2B, mask, reinterpret_cast<float4 *>(lam),
+    k_scatter_target_df<<<B, 128, 0, s>>>(t, cols, wts, log2B, mask, reinterpret_cast<float4 *>(lam),
                                           reinterpret_cast<const float4 *>(psi_final), fpart);
 }
 

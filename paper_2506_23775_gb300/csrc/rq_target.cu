@@ -75,12 +75,15 @@ __global__ void k_cheb_step(const TargetDev t, int S, long long total, const dou
     }
 }
 
-// One CTA per column b: lambda[x, b] = U[x, j_b] over the sector of j_b and
-// fpart[b] = -Re sum_x conj(U[x, j_b]) psi_N[x, b].
-__global__ void k_scatter_target(const TargetDev t, const int32_t *cols, int log2B, long long mask,
-                                 double2 *lam, const double2 *psi, double *fpart) {
+// One CTA per column b: lambda[x, b] = w_b U[x, j_b] over the sector of j_b and
+// fpart[b] = -w_b Re sum_x conj(U[x, j_b]) psi_N[x, b]; w_b = 1 unless the
+// columns are weighted orbit representatives (wts != NULL).  Everything the
+// backward pass computes is linear in lambda, so the weight carries through.
+__global__ void k_scatter_target(const TargetDev t, const int32_t *cols, const double *wts, int log2B,
+                                 long long mask, double2 *lam, const double2 *psi, double *fpart) {
     const int b = blockIdx.x;
     const int j = cols[b];
+    const double wb = wts ? wts[b] : 1.0;
     double acc = 0.0;
     if (j >= 0) {
         const int s = t.sec_of[j];
@@ -89,7 +92,7 @@ __global__ void k_scatter_target(const TargetDev t, const int32_t *cols, int log
         const int32_t *bas = t.basis + t.off_basis[s];
         for (long long r = threadIdx.x; r < m; r += blockDim.x) {
             const long long o = (((long long)bas[r] & mask) << log2B) | b;
-            const double2 u = ucol[r];
+            const double2 u = make_double2(wb * ucol[r].x, wb * ucol[r].y);
             const double2 p = psi[o];
             lam[o] = u;
             acc = fma(u.x, p.x, acc);
@@ -126,11 +129,11 @@ void launch_cheb_step(const TargetDev &t, int n_sectors, long long total, const 
         hop_scale, bond_masks, n_bonds, L, U);
 }
 
-void launch_scatter_target(const TargetDev &t, const int32_t *cols, int B, int log2B,
+void launch_scatter_target(const TargetDev &t, const int32_t *cols, const double *wts, int B, int log2B,
                            int parity_layout, int n, double2 *lam, const double2 *psi_final,
                            double *fpart, cudaStream_t s) {
     const long long mask = parity_layout ? ((1LL << (n - 1)) - 1) : ((1LL << n) - 1);
-    k_scatter_target<<<B, 128, 0, s>>>(t, cols, log2B, mask, lam, psi_final, fpart);
+    k_scatter_target<<<B, 128, 0, s>>>(t, cols, wts, log2B, mask, lam, psi_final, fpart);
 }
 
 // Bessel functions J_0..J_kmax(x), x >= 0, by Miller's backward recurrence
