@@ -106,6 +106,8 @@ typedef struct {
     int accepted;
     int n_inner;
     int tcg_exit;
+    int full_hessian;   /* in: 1 = compute the full Hessian once (rq_hessian) and run
+                           tCG on it on the host; 0 = one device HVP per tCG step */
 } rq_tr_state;
 
 /* Sizes and counters of a set-up context (diagnostics and benchmarking). */
@@ -148,6 +150,24 @@ rq_status rq_set_columns(rq_ctx *ctx, int64_t col_begin, int64_t col_end);
  * HVP directions swept together (1..4, 0 = automatic).  Reallocates the
  * workspace; RQ_ENOMEM if it does not fit. */
 rq_status rq_set_tile(rq_ctx *ctx, int columns_per_tile, int max_dirs);
+
+/* Full Hessian (paper Sec. "Efficient gradient and Hessian computation",
+ * Fig. hole_application, Fig. hessian_pass_second_gradient): forward and
+ * backward pass keeping every state, then for each gate l the hole of G_l
+ * applied to psi_{l-1} (a state-vector array with one member per gate entry,
+ * 8 for parity gates) propagated through the later gates and contracted at
+ * every later gate l'.  Returns, over the column range, f, the Euclidean
+ * gradient gbar = d_x f + i d_y f (Eq. def_grad; egrad [n_params][4][4],
+ * masked for parity gates; may be NULL) and the holomorphic second
+ * derivatives of F = Tr[U^dagger C(G)] (f = -Re F) with tied copies summed:
+ * hess[(p*16 + a*4 + b) * D + (q*16 + c*4 + d)] = d^2 F / dG_p[a,b] dG_q[c,d],
+ * complex128, D = 16 n_params (symmetric; zero outside the parity pattern).
+ * The real Hessian of f in (Re, Im) coordinates is [[-Re H, Im H], [Im H,
+ * Re H]], and the Euclidean HVP along X is -conj(H vec(X)).  Runs in FP64
+ * whatever rq_set_arithmetic says; allocates (g + 2 * members) tiles of
+ * temporaries for the call (RQ_ENOMEM if they do not fit: lower the tile
+ * size).  Cost per tile ~ 16 g^2 / 2 gate passes (8 g^2 / 2 for parity). */
+rq_status rq_hessian(rq_ctx *ctx, const double *gates, double *f, double *egrad, double *hess);
 
 /* Translation-representative basis sums (paper Sec. "Exploiting
  * translational invariance", applied here to the basis sum).  If the chain is

@@ -909,6 +909,175 @@ rq_status rq_set_tile(rq_ctx *ctx, int columns_per_tile, int max_dirs) {
     return rebuild_tiles(ctx);
 }
 
+rq_status rq_hessian(rq_ctx *ctx, const double *gates, double *f, double *egrad, double *hess) {
+    if (!ctx) return RQ_EINVAL;
+    if (!ctx->ready) return fail(ctx, RQ_ESTATE, "no target set up");
+    if (!gates || !hess) return fail(ctx, RQ_EINVAL, "gates or hess is NULL");
+    RQ_TRY(ensure_small(ctx, 1));
+    cudaStream_t s = ctx->stream;
+    const int g = ctx->g, P = ctx->P, B = ctx->B;
+    const int log2M = ctx->structure == 1 ? 3 : 4, M = 1 << log2M;
+    const long long tile = ctx->n_store * B;
+    // temporaries: adjoint checkpoints, two member arrays, partials, block accumulators
+    long long tmp_bytes = 0;
+    double2 *lamck = nullptr, *arr0 = nullptr, *arr1 = nullptr;
+    double *hpart = nullptr, *hacc = nullptr;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(s);
+        dev_free(lamck);
+        dev_free(arr0);
+        dev_free(arr1);
+        dev_free(hpart);
+        dev_free(hacc);
+    };
+    rq_status st = dev_alloc(ctx, &lamck, tile * g, tmp_bytes);
+    if (st == RQ_OK) st = dev_alloc(ctx, &arr0, tile * M, tmp_bytes);
+    if (st == RQ_OK) st = dev_alloc(ctx, &arr1, tile * M, tmp_bytes);
+    if (st == RQ_OK) st = dev_alloc(ctx, &hpart, (long long)g * M * ctx->ncta * rq::kEnvDoubles, tmp_bytes);
+    if (st == RQ_OK) st = dev_alloc(ctx, &hacc, (long long)g * g * M * rq::kEnvDoubles, tmp_bytes);
+    if (st != RQ_OK) {
+        cleanup();
+        return st;
+    }
+#define RQH_CUDA(call)                                                                            \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            cleanup();                                                                            \
+            return fail(ctx, RQ_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));                 \
+        }                                                                                         \
+    } while (0)
+#define RQH_LAUNCHED() RQH_CUDA((++ctx->launches, cudaGetLastError()))
+    RQH_CUDA(cudaMemcpyAsync(ctx->d_in_gates, gates, sizeof(double2) * 16 * P, cudaMemcpyHostToDevice, s));
+    rq::launch_mask_gates(ctx->d_in_gates, ctx->d_gates, P, ctx->structure, s);
+    RQH_LAUNCHED();
+    RQH_CUDA(cudaMemsetAsync(hacc, 0, sizeof(double) * g * g * M * rq::kEnvDoubles, s));
+    RQH_CUDA(cudaMemsetAsync(ctx->d_env, 0, sizeof(double) * g * rq::kEnvDoubles, s));
+    RQH_CUDA(cudaMemsetAsync(ctx->d_facc, 0, sizeof(double), s));
+    for (int ti = 0; ti < ctx->n_tiles; ++ti) {
+        const int32_t *cols = ctx->d_cols + (long long)ti * B;
+        const double *wts = ctx->tshift > 0 ? ctx->d_wts + (long long)ti * B : nullptr;
+        const int par = ctx->tile_parity[ti];
+        RQH_CUDA(cudaMemsetAsync(ctx->d_psi, 0, sizeof(double2) * tile, s));
+        rq::launch_init_unit(ctx->d_psi, cols, B, ctx->log2B, ctx->n_store, ctx->structure, s);
+        RQH_LAUNCHED();
+        for (int l = 0; l < g; ++l) {  // forward pass with checkpoints
+            const GateGeom &geo = ctx->geo[l];
+            rq::FwdArgs a{};
+            a.psi_in = ctx->d_psi + l * tile;
+            a.psi_out = ctx->d_psi + (l + 1) * tile;
+            a.kdirs = 0;
+            a.gate = ctx->d_gates + (long long)geo.param * 16;
+            a.geo = geo;
+            a.log2B = ctx->log2B;
+            a.tile_parity = par;
+            a.n_items = (geo.mode == rq::kParity2 ? ctx->n_store / 2 : ctx->n_store / 4) * B;
+            rq::launch_fwd(a, ctx->ncta, s);
+            RQH_LAUNCHED();
+        }
+        RQH_CUDA(cudaMemsetAsync(ctx->d_lam, 0, sizeof(double2) * tile, s));
+        rq::launch_scatter_target(target_dev(ctx), cols, wts, B, ctx->log2B, ctx->structure, ctx->n, ctx->d_lam,
+                                  ctx->d_psi + g * tile, ctx->d_fpart, s);
+        RQH_LAUNCHED();
+        rq::launch_reduce_f(ctx->d_fpart, B, ctx->d_facc, s);
+        RQH_LAUNCHED();
+        for (int l = g - 1; l >= 0; --l) {  // backward pass, keeping every lambda_l
+            const GateGeom &geo = ctx->geo[l];
+            RQH_CUDA(cudaMemcpyAsync(lamck + l * tile, ctx->d_lam, sizeof(double2) * tile, cudaMemcpyDeviceToDevice, s));
+            rq::BwdArgs a{};
+            a.lam = ctx->d_lam;
+            a.psi = ctx->d_psi + l * tile;
+            a.gate = ctx->d_gates + (long long)geo.param * 16;
+            a.geo = geo;
+            a.log2B = ctx->log2B;
+            a.tile_parity = par;
+            a.update = l > 0 ? 1 : 0;
+            a.accumulate = 1;
+            a.n_items = (geo.mode == rq::kParity2 ? ctx->n_store / 2 : ctx->n_store / 4) * B;
+            a.part = ctx->d_part + (long long)l * ctx->ncta * rq::kEnvDoubles;
+            rq::launch_bwd_base(a, ctx->ncta, s);
+            RQH_LAUNCHED();
+        }
+        rq::launch_reduce_env(ctx->d_part, ctx->ncta, g, ctx->d_env, s);
+        RQH_LAUNCHED();
+        // second forward passes: hole of gate l, propagated and contracted at every l' > l
+        for (int l = 0; l + 1 < g; ++l) {
+            const GateGeom &geo = ctx->geo[l];
+            const long long items_l = (geo.mode == rq::kParity2 ? ctx->n_store / 2 : ctx->n_store / 4) * B;
+            rq::launch_hole_apply(ctx->d_psi + l * tile, arr0, geo, ctx->log2B, log2M, ctx->structure, par, items_l,
+                                  ctx->ncta, s);
+            RQH_LAUNCHED();
+            double2 *cur = arr0, *nxt = arr1;
+            for (int lp = l + 1; lp < g; ++lp) {
+                const GateGeom &gp = ctx->geo[lp];
+                const long long items = (gp.mode == rq::kParity2 ? ctx->n_store / 2 : ctx->n_store / 4) * B;
+                rq::launch_array_env(lamck + lp * tile, cur, gp, ctx->log2B, log2M, par, items, ctx->ncta,
+                                     hpart + (long long)lp * M * ctx->ncta * rq::kEnvDoubles, s);
+                RQH_LAUNCHED();
+                if (lp + 1 < g) {
+                    rq::FwdArgs a{};
+                    a.psi_in = cur;
+                    a.psi_out = nxt;
+                    a.kdirs = 0;
+                    a.gate = ctx->d_gates + (long long)gp.param * 16;
+                    a.geo = gp;
+                    a.log2B = ctx->log2B + log2M;
+                    a.tile_parity = par;
+                    a.n_items = items * M;
+                    rq::launch_fwd(a, ctx->ncta, s);
+                    RQH_LAUNCHED();
+                    std::swap(cur, nxt);
+                }
+            }
+            rq::launch_reduce_rows(hpart + (long long)(l + 1) * M * ctx->ncta * rq::kEnvDoubles, ctx->ncta,
+                                   (long long)(g - 1 - l) * M, hacc + ((long long)l * g + l + 1) * M * rq::kEnvDoubles, s);
+            RQH_LAUNCHED();
+        }
+    }
+    // f and the Euclidean gradient (masked), then the blocks to the host
+    const int saved_space = ctx->space;
+    ctx->space = 1;
+    rq::launch_geometry(ctx->d_gates, ctx->d_dirs, ctx->d_env, ctx->d_envd, ctx->d_param_of, g, P, 0, ctx->structure,
+                        1, ctx->d_facc, ctx->d_out, reinterpret_cast<double2 *>(ctx->d_out + 2), nullptr, s);
+    ctx->space = saved_space;
+    RQH_LAUNCHED();
+    std::vector<double> hb((size_t)g * g * M * rq::kEnvDoubles);
+    double fh = 0.0;
+    std::vector<double> eg((size_t)P * 32);
+    RQH_CUDA(cudaMemcpyAsync(hb.data(), hacc, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, s));
+    RQH_CUDA(cudaMemcpyAsync(&fh, ctx->d_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    RQH_CUDA(cudaMemcpyAsync(eg.data(), ctx->d_out + 2, sizeof(double) * eg.size(), cudaMemcpyDeviceToHost, s));
+    RQH_CUDA(cudaStreamSynchronize(s));
+#undef RQH_LAUNCHED
+#undef RQH_CUDA
+    cleanup();
+    if (f) *f = fh;
+    if (egrad) std::memcpy(egrad, eg.data(), sizeof(double) * eg.size());
+    // tied, symmetric assembly: H[p(l) ab][p(l') cd] += block and its transpose
+    static const int members[2][16][2] = {
+        {{0, 0}, {0, 1}, {0, 2}, {0, 3}, {1, 0}, {1, 1}, {1, 2}, {1, 3},
+         {2, 0}, {2, 1}, {2, 2}, {2, 3}, {3, 0}, {3, 1}, {3, 2}, {3, 3}},
+        {{0, 0}, {0, 3}, {3, 0}, {3, 3}, {1, 1}, {1, 2}, {2, 1}, {2, 2},
+         {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}}};
+    const long long D = (long long)P * 16;
+    std::memset(hess, 0, sizeof(double) * 2 * D * D);
+    for (int l = 0; l < g; ++l)
+        for (int lp = l + 1; lp < g; ++lp)
+            for (int m = 0; m < M; ++m) {
+                const double *blk = hb.data() + (((long long)l * g + lp) * M + m) * rq::kEnvDoubles;
+                const long long row = (long long)ctx->param_of[l] * 16 + members[ctx->structure][m][0] * 4 +
+                                      members[ctx->structure][m][1];
+                for (int cd = 0; cd < 16; ++cd) {
+                    const long long col = (long long)ctx->param_of[lp] * 16 + cd;
+                    hess[2 * (row * D + col)] += blk[2 * cd];
+                    hess[2 * (row * D + col) + 1] += blk[2 * cd + 1];
+                    hess[2 * (col * D + row)] += blk[2 * cd];
+                    hess[2 * (col * D + row) + 1] += blk[2 * cd + 1];
+                }
+            }
+    return RQ_OK;
+}
+
 rq_status rq_set_translation(rq_ctx *ctx, int shift_sites) {
     if (!ctx) return RQ_EINVAL;
     if (!ctx->ready) return fail(ctx, RQ_ESTATE, "no target set up");

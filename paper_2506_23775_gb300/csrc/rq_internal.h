@@ -104,6 +104,13 @@ void launch_cheb_step(const TargetDev &t, int n_sectors, long long total, const 
 void launch_cheb_init(const long long *off_u, const long long *sizes, int n_sectors, long long total,
                       double *prev, double2 *acc, double2 c0, cudaStream_t s);
 
+// Launchers (rq_hessian.cu).
+void launch_hole_apply(const double2 *psi, double2 *arr, const GateGeom &geo, int log2B, int log2M,
+                       int parity_members, int tile_parity, long long n_items, int grid, cudaStream_t s);
+void launch_array_env(const double2 *lam, const double2 *arr, const GateGeom &geo, int log2B, int log2M,
+                      int tile_parity, long long n_items, int ncta, double *part, cudaStream_t s);
+void launch_reduce_rows(const double *part, int ncta, long long rows, double *hacc, cudaStream_t s);
+
 // Launchers (rq_geometry.cu).
 void launch_reduce_env(const double *part, int ncta, int n_gates, double *env, cudaStream_t s);
 void launch_reduce_f(const double *fpart, int B, double *facc, cudaStream_t s);

@@ -8,6 +8,7 @@
 #include "rq_internal.h"
 
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <vector>
 
@@ -71,6 +72,62 @@ bool inv4(const double *A, double *Ainv) {
     return true;
 }
 
+using C4 = std::complex<double>;
+
+void load4(const double *p, C4 (&m)[16]) {
+    for (int i = 0; i < 16; ++i) m[i] = C4(p[2 * i], p[2 * i + 1]);
+}
+
+void store4(const C4 (&m)[16], double *p) {
+    for (int i = 0; i < 16; ++i) {
+        p[2 * i] = m[i].real();
+        p[2 * i + 1] = m[i].imag();
+    }
+}
+
+// A^dagger B
+void mul_dag(const C4 (&A)[16], const C4 (&B)[16], C4 (&C)[16]) {
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            C4 s = 0;
+            for (int k = 0; k < 4; ++k) s += std::conj(A[k * 4 + i]) * B[k * 4 + j];
+            C[i * 4 + j] = s;
+        }
+}
+
+void mul(const C4 (&A)[16], const C4 (&B)[16], C4 (&C)[16]) {
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            C4 s = 0;
+            for (int k = 0; k < 4; ++k) s += A[i * 4 + k] * B[k * 4 + j];
+            C[i * 4 + j] = s;
+        }
+}
+
+// (A - A^dagger)/2 (sign -1) or (A + A^dagger)/2 (sign +1)
+void herm(const C4 (&A)[16], double sign, C4 (&C)[16]) {
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) C[i * 4 + j] = 0.5 * (A[i * 4 + j] + sign * std::conj(A[j * 4 + i]));
+}
+
+bool in_pattern(int e) {
+    const int r = e >> 2, c = e & 3;
+    return (r == 0 || r == 3) == (c == 0 || c == 3);
+}
+
+// P_G(Z) = G skew(G^dagger Z) for every parameter gate
+void project_all(const double *G, const Vec &Z, Vec &out, int P) {
+    for (int p = 0; p < P; ++p) {
+        C4 g[16], z[16], t[16], s[16], r[16];
+        load4(G + p * 32, g);
+        load4(Z.data() + p * 32, z);
+        mul_dag(g, z, t);
+        herm(t, -1.0, s);
+        mul(g, s, r);
+        store4(r, out.data() + p * 32);
+    }
+}
+
 }  // namespace
 
 namespace rq {
@@ -125,8 +182,57 @@ extern "C" rq_status rq_tr_step(rq_ctx *ctx, double *gates, rq_tr_state *st) {
 
     Vec grad(dimv), eta(dimv, 0.0), Heta(dimv, 0.0), r(dimv), delta(dimv), Hd(dimv);
     double f = 0.0;
-    rq_status s = rq::eval_host(ctx, gates, nullptr, 0, 1, &f, grad.data(), nullptr);
-    if (s != RQ_OK) return s;
+    rq_status s = RQ_OK;
+    // full-Hessian mode: gbar, the tied holomorphic Hessian H and the
+    // correction matrices sym(G^dagger gbar), once per step
+    const bool full = st->full_hessian != 0;
+    const long long D = (long long)P * 16;
+    std::vector<double> Hh;
+    Vec gbar;
+    std::vector<C4> symm;
+    if (full) {
+        Hh.resize((size_t)(2 * D * D));
+        gbar.resize(dimv);
+        s = rq_hessian(ctx, gates, &f, gbar.data(), Hh.data());
+        if (s != RQ_OK) return s;
+        project_all(gates, gbar, grad, P);
+        symm.resize((size_t)P * 16);
+        for (int p = 0; p < P; ++p) {
+            C4 g4[16], b4[16], m4[16], s4[16];
+            load4(gates + p * 32, g4);
+            load4(gbar.data() + p * 32, b4);
+            mul_dag(g4, b4, m4);
+            herm(m4, +1.0, s4);
+            for (int i = 0; i < 16; ++i) symm[(size_t)p * 16 + i] = s4[i];
+        }
+    } else {
+        s = rq::eval_host(ctx, gates, nullptr, 0, 1, &f, grad.data(), nullptr);
+        if (s != RQ_OK) return s;
+    }
+    // Riemannian Hessian of the tangent vector X from H:
+    // P_G( mask(-conj(H vec X)) - X sym(G^dagger gbar) )
+    auto hess_full = [&](const Vec &X, Vec &out) {
+        Vec dg(dimv, 0.0);
+        for (long long i = 0; i < D; ++i) {
+            C4 acc = 0;
+            const double *row = Hh.data() + 2 * i * D;
+            for (long long j = 0; j < D; ++j) acc += C4(row[2 * j], row[2 * j + 1]) * C4(X[2 * j], X[2 * j + 1]);
+            const bool keep = info.structure != 1 || in_pattern((int)(i & 15));
+            dg[2 * i] = keep ? -acc.real() : 0.0;
+            dg[2 * i + 1] = keep ? acc.imag() : 0.0;
+        }
+        for (int p = 0; p < P; ++p) {
+            C4 x4[16], s4[16], xs[16];
+            load4(X.data() + p * 32, x4);
+            for (int i = 0; i < 16; ++i) s4[i] = symm[(size_t)p * 16 + i];
+            mul(x4, s4, xs);
+            for (int i = 0; i < 16; ++i) {
+                dg[p * 32 + 2 * i] -= xs[i].real();
+                dg[p * 32 + 2 * i + 1] -= xs[i].imag();
+            }
+        }
+        project_all(gates, dg, out, P);
+    };
     r = grad;
     for (size_t i = 0; i < dimv; ++i) delta[i] = -r[i];
     double rr = dot(r, r);
@@ -135,10 +241,14 @@ extern "C" rq_status rq_tr_step(rq_ctx *ctx, double *gates, rq_tr_state *st) {
     // truncated CG (Steihaug); Hess applied by the device HVP
     for (j = 0; j < max_inner; ++j) {
         if (rr == 0.0) { code = 0; break; }
-        double fh = 0.0;
-        // the gradient environments at these gates are still in the accumulators
-        s = rq::eval_host(ctx, gates, delta.data(), 1, 2, &fh, nullptr, Hd.data());
-        if (s != RQ_OK) return s;
+        if (full) {
+            hess_full(delta, Hd);
+        } else {
+            double fh = 0.0;
+            // the gradient environments at these gates are still in the accumulators
+            s = rq::eval_host(ctx, gates, delta.data(), 1, 2, &fh, nullptr, Hd.data());
+            if (s != RQ_OK) return s;
+        }
         const double dHd = dot(delta, Hd);
         auto to_boundary = [&]() {
             const double a = dot(delta, delta), b = 2.0 * dot(eta, delta), c = dot(eta, eta) - radius * radius;

@@ -24,7 +24,7 @@ EXPORTS = ("rq_create", "rq_destroy", "rq_setup_target", "rq_set_columns", "rq_s
            "rq_tr_step", "rq_target_column", "rq_get_info", "rq_profile_start", "rq_profile_stop",
            "rq_cost_static", "rq_set_gradient_space", "rq_batch_create", "rq_batch_destroy",
            "rq_batch_add", "rq_batch_set_tile", "rq_batch_hvp", "rq_batch_info", "rq_batch_last_error",
-           "rq_set_arithmetic", "rq_set_translation", "rq_last_error")
+           "rq_set_arithmetic", "rq_set_translation", "rq_hessian", "rq_last_error")
 
 
 class RQCircuit(C.Structure):
@@ -43,7 +43,7 @@ class RQTRState(C.Structure):
                 ("kappa", C.c_double), ("theta", C.c_double), ("max_inner", C.c_int),
                 ("f", C.c_double), ("f_new", C.c_double), ("rho", C.c_double),
                 ("grad_norm", C.c_double), ("step_norm", C.c_double), ("accepted", C.c_int),
-                ("n_inner", C.c_int), ("tcg_exit", C.c_int)]
+                ("n_inner", C.c_int), ("tcg_exit", C.c_int), ("full_hessian", C.c_int)]
 
 
 class RQInfo(C.Structure):
@@ -95,6 +95,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "rq_set_gradient_space": ([vp, C.c_int], C.c_int),
         "rq_set_arithmetic": ([vp, C.c_int], C.c_int),
         "rq_set_translation": ([vp, C.c_int], C.c_int),
+        "rq_hessian": ([vp, dp, dp, dp, dp], C.c_int),
         "rq_batch_create": ([C.POINTER(vp), C.c_int], C.c_int),
         "rq_batch_destroy": ([vp], C.c_int),
         "rq_batch_add": ([vp, C.POINTER(RQTarget), C.POINTER(RQCircuit), C.POINTER(C.c_int)], C.c_int),
@@ -286,14 +287,28 @@ class Context:
                                            flops=arr[i].flops, bytes=arr[i].bytes)
                 for i in range(min(n.value, 16))}
 
+    def hessian(self, gates):
+        """``(f, egrad, H)``: Euclidean gradient and the tied holomorphic
+        second derivatives ``H[(p,a,b), (q,c,d)]`` as a ``[16P, 16P]`` array."""
+        g = _c128(gates)
+        eg = np.empty_like(g)
+        D = g.shape[0] * 16
+        H = np.empty((D, D), dtype=np.complex128)
+        f = C.c_double()
+        self._check(self._lib.rq_hessian(self._h, _dptr(g.view(np.float64)), C.byref(f),
+                                         _dptr(eg.view(np.float64)), _dptr(H.view(np.float64))))
+        return f.value, eg, H
+
     def target_column(self, j: int) -> np.ndarray:
         out = np.empty(1 << self.n_qubits, dtype=np.complex128)
         self._check(self._lib.rq_target_column(self._h, int(j), _dptr(out.view(np.float64))))
         return out
 
 
-def tr_state(radius=0.01, max_radius=0.1, rho_accept=0.125, kappa=0.1, theta=1.0, max_inner=0) -> RQTRState:
+def tr_state(radius=0.01, max_radius=0.1, rho_accept=0.125, kappa=0.1, theta=1.0, max_inner=0,
+             full_hessian=False) -> RQTRState:
     s = RQTRState()
+    s.full_hessian = 1 if full_hessian else 0
     s.radius, s.max_radius, s.rho_accept = radius, max_radius, rho_accept
     s.kappa, s.theta, s.max_inner = kappa, theta, max_inner
     return s
