@@ -73,8 +73,10 @@ typedef struct {
 /* Target U = exp(-i H t).  model 0: spinful Fermi-Hubbard chain (Eq. sfFH)
  * on n_sites sites, qubit j = (site j, up), qubit n_sites + j = (site j,
  * down), hopping -J on nearest-neighbour bonds of each spin chain (plus the
- * wrap bond without Z string when periodic, Eq. slFH_qubit), on-site U.
- * n_qubits of the circuit must equal 2 * n_sites. */
+ * wrap bond without Z string when periodic, Eq. slFH_qubit), on-site U;
+ * n_qubits = 2 * n_sites.  model 1: spinless chain in its hard-core boson
+ * form (Eq. slFH_qubit): hopping -J and nearest-neighbour interaction
+ * U n_j n_{j+1} on every bond (wrap bond if periodic); n_qubits = n_sites. */
 typedef struct {
     int model;
     int n_sites;

@@ -47,8 +47,12 @@ def chain_bonds(L: int, periodic: bool) -> List[Tuple[int, int]]:
     return bonds
 
 
-def hamiltonian_dense(L: int, J: float, U: float, periodic: bool = False) -> np.ndarray:
-    """Eq. sfFH as a dense real ``2^n x 2^n`` matrix, built term by term."""
+def hamiltonian_dense(L: int, J: float, U: float, periodic: bool = False, model: int = 0) -> np.ndarray:
+    """Dense real matrix built term by term: Eq. sfFH (model 0, n = 2L) or
+    the spinless chain of Sec. "Model system and circuit topology" with its
+    wrap bond in hard-core boson form, Eq. slFH_qubit (model 1, n = L)."""
+    if model == 1:
+        return _hamiltonian_dense_spinless(L, J, U, periodic)
     n = 2 * L
     dim = 1 << n
     H = np.zeros((dim, dim))
@@ -65,6 +69,20 @@ def hamiltonian_dense(L: int, J: float, U: float, periodic: bool = False) -> np.
     return H
 
 
+def _hamiltonian_dense_spinless(L: int, J: float, U: float, periodic: bool) -> np.ndarray:
+    n = L
+    H = np.zeros((1 << n, 1 << n))
+    for (i, k) in chain_bonds(L, periodic):
+        wrap = periodic and (i, k) == (L - 1, 0)
+        op = hardcore_annihilator if wrap else jw_annihilator
+        ai, ak = op(i, n), op(k, n)
+        H += -J * (ai.T @ ak + ak.T @ ai)
+        ni = jw_annihilator(i, n)
+        nk = jw_annihilator(k, n)
+        H += U * (ni.T @ ni) @ (nk.T @ nk)
+    return H
+
+
 def target_unitary_dense(H: np.ndarray, t: float) -> np.ndarray:
     """``exp(-i H t)`` for real symmetric ``H`` via its eigendecomposition."""
     w, V = np.linalg.eigh(H)
@@ -78,16 +96,21 @@ def bit(x, q: int, n: int):
     return (x >> (n - 1 - q)) & 1
 
 
-def sector_label(x: int, L: int) -> Tuple[int, int]:
-    """``(N_up, N_down)`` of basis state ``x``."""
+def sector_label(x: int, L: int, model: int = 0):
+    """``(N_up, N_down)`` of basis state ``x`` (model 1: ``(N,)``)."""
+    if model == 1:
+        return (bin(int(x)).count("1"),)
     n = 2 * L
     up = sum(bit(x, q, n) for q in range(L))
     dn = sum(bit(x, q, n) for q in range(L, n))
     return up, dn
 
 
-def sector_basis(L: int, label: Tuple[int, int]) -> np.ndarray:
-    """Ascending basis indices of one ``(N_up, N_down)`` sector."""
+def sector_basis(L: int, label, model: int = 0) -> np.ndarray:
+    """Ascending basis indices of one sector."""
+    if model == 1:
+        xs = np.arange(1 << L)
+        return xs[np.array([bin(int(x)).count("1") for x in xs]) == label[0]]
     n = 2 * L
     xs = np.arange(1 << n)
     up = sum(bit(xs, q, n) for q in range(L))
@@ -100,7 +123,7 @@ def sector_size(L: int, label: Tuple[int, int]) -> int:
 
 
 def hamiltonian_sector(L: int, J: float, U: float, periodic: bool,
-                       label: Tuple[int, int]) -> Tuple[np.ndarray, np.ndarray]:
+                       label, model: int = 0) -> Tuple[np.ndarray, np.ndarray]:
     """Matrix of Eq. sfFH on one sector, from its action on basis states.
 
     A hop along a bond ``(p, q)`` of one spin chain exchanges an occupied and
@@ -108,6 +131,8 @@ def hamiltonian_sector(L: int, J: float, U: float, periodic: bool,
     up-first ordering carry no Z string, the wrap bond is hard-core); the
     diagonal is ``U`` times the number of doubly occupied sites.
     """
+    if model == 1:
+        return _hamiltonian_sector_spinless(L, J, U, periodic, label)
     n = 2 * L
     basis = sector_basis(L, label)
     pos = {int(x): i for i, x in enumerate(basis)}
@@ -123,6 +148,26 @@ def hamiltonian_sector(L: int, J: float, U: float, periodic: bool,
     return H, basis
 
 
+def _hamiltonian_sector_spinless(L, J, U, periodic, label):
+    """Spinless chain on one particle-number sector: a hop along a bond
+    exchanges an occupied and an empty site with amplitude -J; the diagonal is
+    U times the number of bonds with both sites occupied."""
+    n = L
+    basis = sector_basis(L, label, model=1)
+    pos = {int(x): i for i, x in enumerate(basis)}
+    H = np.zeros((len(basis), len(basis)))
+    for i, x in enumerate(basis):
+        x = int(x)
+        for (p, q) in chain_bonds(L, periodic):
+            bp, bq = bit(x, p, n), bit(x, q, n)
+            if bp and bq:
+                H[i, i] += U
+            elif bp != bq:
+                y = x ^ (1 << (n - 1 - p)) ^ (1 << (n - 1 - q))
+                H[pos[y], i] += -J
+    return H, basis
+
+
 class SectorTarget:
     """``U = exp(-iHt)`` columns, assembled from per-sector eigendecompositions.
 
@@ -130,20 +175,20 @@ class SectorTarget:
     sector blocks are computed on first use and cached.
     """
 
-    def __init__(self, L: int, J: float, U: float, t: float, periodic: bool = False):
-        self.L, self.J, self.U, self.t, self.periodic = L, J, U, t, periodic
-        self.n = 2 * L
+    def __init__(self, L: int, J: float, U: float, t: float, periodic: bool = False, model: int = 0):
+        self.L, self.J, self.U, self.t, self.periodic, self.model = L, J, U, t, periodic, model
+        self.n = 2 * L if model == 0 else L
         self._blocks: Dict[Tuple[int, int], Tuple[np.ndarray, Dict[int, int], np.ndarray]] = {}
 
     def block(self, label):
         if label not in self._blocks:
-            H, basis = hamiltonian_sector(self.L, self.J, self.U, self.periodic, label)
+            H, basis = hamiltonian_sector(self.L, self.J, self.U, self.periodic, label, self.model)
             Us = target_unitary_dense(H, self.t)
             self._blocks[label] = (basis, {int(x): i for i, x in enumerate(basis)}, Us)
         return self._blocks[label]
 
     def column(self, j: int) -> np.ndarray:
-        basis, pos, Us = self.block(sector_label(int(j), self.L))
+        basis, pos, Us = self.block(sector_label(int(j), self.L, self.model))
         v = np.zeros(1 << self.n, dtype=np.complex128)
         v[basis] = Us[:, pos[int(j)]]
         return v

@@ -383,14 +383,16 @@ rq::TargetDev target_dev(const rq_ctx *ctx) {
 
 // Build the per-sector target blocks on the device (Chebyshev expansion).
 rq_status build_target(rq_ctx *ctx) {
-    const int n = ctx->n, L = ctx->L;
+    const int n = ctx->n, L = ctx->L, model = ctx->tgt.model;
     const long long dim = 1LL << n, lowmask = (1LL << L) - 1;
-    ctx->S = (L + 1) * (L + 1);
+    // conserved labels: (N_up, N_down) for the spinful chain, N for the spinless one
+    ctx->S = model == 0 ? (L + 1) * (L + 1) : L + 1;
     std::vector<long long> count(ctx->S, 0);
     ctx->sec_of_h.assign(dim, 0);
     ctx->pos_h.assign(dim, 0);
     for (long long x = 0; x < dim; ++x) {
-        const int s = __builtin_popcountll(x >> L) * (L + 1) + __builtin_popcountll(x & lowmask);
+        const int s = model == 0 ? __builtin_popcountll(x >> L) * (L + 1) + __builtin_popcountll(x & lowmask)
+                                  : __builtin_popcountll(x);
         ctx->sec_of_h[x] = s;
         ctx->pos_h[x] = (int32_t)count[s]++;
     }
@@ -405,18 +407,28 @@ rq_status build_target(rq_ctx *ctx) {
     ctx->u_entries = ctx->off_u[ctx->S];
     std::vector<long long> sizes(count.begin(), count.end());
 
-    // hopping bonds of both spin chains as bit masks (qubit q <-> bit n-1-q)
+    // hopping bonds as bit masks (qubit q <-> bit n-1-q): both spin chains
+    // (spinful) or the one chain (spinless), plus the wrap bond if periodic
     std::vector<long long> bonds;
-    for (int off = 0; off <= L; off += L) {
+    const int n_chains = model == 0 ? 2 : 1;
+    for (int ch = 0; ch < n_chains; ++ch) {
+        const int off = ch * L;
         for (int j = 0; j + 1 < L; ++j)
             bonds.push_back((1LL << (n - 1 - off - j)) | (1LL << (n - 2 - off - j)));
         if (ctx->tgt.periodic && L > 2) bonds.push_back((1LL << (n - 1 - off - (L - 1))) | (1LL << (n - 1 - off)));
     }
+    // diagonal: U n_up n_down on every site (spinful), U n_j n_{j+1} on every bond (spinless)
+    auto diag_of = [&](long long x) {
+        if (model == 0) return ctx->tgt.U * (double)__builtin_popcountll((x >> L) & (x & lowmask));
+        int both = 0;
+        for (long long mk : bonds) both += (x & mk) == mk;
+        return ctx->tgt.U * both;
+    };
     // Gershgorin interval of H
     const double J = ctx->tgt.J, U = ctx->tgt.U, t = ctx->tgt.t;
     double emin = 1e300, emax = -1e300;
     for (long long x = 0; x < dim; ++x) {
-        const double diag = U * (double)__builtin_popcountll((x >> L) & (x & lowmask));
+        const double diag = diag_of(x);
         int flips = 0;
         for (long long mk : bonds) {
             const long long bits = x & mk;
@@ -485,10 +497,10 @@ rq_status build_target(rq_ctx *ctx) {
         for (int k = 1; k <= K; ++k) {
             if (k == 1) {
                 rq::launch_cheb_step(td, ctx->S, ctx->u_entries, prev, cur, ctx->d_U, coef(1), 1.0, 1,
-                                     dscale, beta, hop, d_bonds, (int)bonds.size(), L, U, ctx->stream);
+                                     dscale, beta, hop, d_bonds, (int)bonds.size(), L, U, model, ctx->stream);
             } else {
                 rq::launch_cheb_step(td, ctx->S, ctx->u_entries, cur, prev, ctx->d_U, coef(k), 2.0, 0,
-                                     dscale, beta, hop, d_bonds, (int)bonds.size(), L, U, ctx->stream);
+                                     dscale, beta, hop, d_bonds, (int)bonds.size(), L, U, model, ctx->stream);
                 std::swap(prev, cur);
             }
             ++ctx->launches;
@@ -810,10 +822,12 @@ rq_status rq_destroy(rq_ctx *ctx) {
 rq_status rq_setup_target(rq_ctx *ctx, const rq_target *tgt, const rq_circuit *c) {
     if (!ctx) return RQ_EINVAL;
     if (!tgt || !c) return fail(ctx, RQ_EINVAL, "target or circuit is NULL");
-    if (tgt->model != 0) return fail(ctx, RQ_EINVAL, "model %d not supported (0: spinful Fermi-Hubbard)", tgt->model);
-    if (tgt->n_sites < 1 || 2 * tgt->n_sites != c->n_qubits || c->n_qubits > rq::kMaxQubits)
-        return fail(ctx, RQ_EINVAL, "n_qubits %d must equal 2 * n_sites (%d) and be <= %d", c->n_qubits,
-                    tgt->n_sites, rq::kMaxQubits);
+    if (tgt->model != 0 && tgt->model != 1)
+        return fail(ctx, RQ_EINVAL, "model %d not supported (0 spinful, 1 spinless Fermi-Hubbard)", tgt->model);
+    const int per_site = tgt->model == 0 ? 2 : 1;
+    if (tgt->n_sites < 1 || per_site * tgt->n_sites != c->n_qubits || c->n_qubits < 2 || c->n_qubits > rq::kMaxQubits)
+        return fail(ctx, RQ_EINVAL, "n_qubits %d must equal %d * n_sites (%d), be >= 2 and <= %d", c->n_qubits,
+                    per_site, tgt->n_sites, rq::kMaxQubits);
     if (!std::isfinite(tgt->J) || !std::isfinite(tgt->U) || !std::isfinite(tgt->t))
         return fail(ctx, RQ_EINVAL, "J, U, t must be finite");
     if (c->n_gates < 1 || !c->pairs) return fail(ctx, RQ_EINVAL, "circuit needs n_gates >= 1 and pairs");
@@ -1091,7 +1105,7 @@ rq_status rq_set_translation(rq_ctx *ctx, int shift_sites) {
     if (shift_sites < 0 || shift_sites >= L || L % shift_sites != 0)
         return fail(ctx, RQ_EINVAL, "shift %d must divide the %d sites and be smaller", shift_sites, L);
     if (!ctx->tgt.periodic) return fail(ctx, RQ_EINVAL, "translation symmetry needs a periodic chain");
-    // qubit map of the shift: site j -> j + s (mod L) on both spin chains
+    // qubit map of the shift: site j -> j + s (mod L) on every chain
     std::vector<int> qmap(n);
     for (int q = 0; q < n; ++q) qmap[q] = (q < L) ? (q + shift_sites) % L : L + (q - L + shift_sites) % L;
     // the circuit must be invariant: in every maximal run of pairwise disjoint

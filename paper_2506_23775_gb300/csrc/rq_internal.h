@@ -100,7 +100,7 @@ void launch_scatter_target(const TargetDev &t, const int32_t *cols, const double
 void launch_cheb_step(const TargetDev &t, int n_sectors, long long total, const double *cur,
                       double *prev_out, double2 *acc, double2 coef, double scale, int first,
                       double diag_scale, double diag_shift, double hop_scale,
-                      const long long *bond_masks, int n_bonds, int L, double U, cudaStream_t s);
+                      const long long *bond_masks, int n_bonds, int L, double U, int model, cudaStream_t s);
 void launch_cheb_init(const long long *off_u, const long long *sizes, int n_sectors, long long total,
                       double *prev, double2 *acc, double2 c0, cudaStream_t s);
 

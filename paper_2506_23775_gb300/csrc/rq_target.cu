@@ -1,10 +1,10 @@
 // Device-resident target U = exp(-iHt) and its use in the sweep.
 //
 // The paper applies U "matrix-free" to each basis column (Sec. "Objective
-// function and matrix-free evaluation") without saying how.  The Fermi-Hubbard
-// H of Eq. sfFH conserves the numbers of up and down particles, so U is block
-// diagonal over (N_up, N_down) sectors and column U|j> lives in the sector of
-// j.  Each block is computed once on the device by the Chebyshev expansion
+// function and matrix-free evaluation") without saying how.  The spinful
+// Fermi-Hubbard H of Eq. sfFH conserves the numbers of up and down particles
+// (the spinless H of Eq. slFH_qubit the particle number), so U is block
+// diagonal over these sectors and column U|j> lives in the sector of j.  Each block is computed once on the device by the Chebyshev expansion
 //     exp(-i H t) = exp(-i b t) sum_k (2 - delta_k0) (-i)^k J_k(a t) T_k(Ht),
 // Ht = (H - b) / a with spectrum in [-1, 1] (Gershgorin bound), applied to the
 // identity of every sector with the sparse H (the Jacobi-Anger expansion; the
@@ -49,7 +49,7 @@ __global__ void k_cheb_init(const long long *off_u, const long long *sizes, int 
 __global__ void k_cheb_step(const TargetDev t, int S, long long total, const double *cur,
                             double *prev_out, double2 *acc, double2 coef, double scale, int first,
                             double dscale, double dshift, double hop, const long long *bonds,
-                            int nb, int L, double U) {
+                            int nb, int L, double U, int model) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long lowmask = (1LL << L) - 1;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
@@ -59,13 +59,15 @@ __global__ void k_cheb_step(const TargetDev t, int S, long long total, const dou
         const long long c = local / m, r = local - c * m;
         const long long col = t.off_u[s] + c * m;
         const long long x = t.basis[t.off_basis[s] + r];
-        const double diag = U * (double)__popcll((x >> L) & (x & lowmask));
-        double h = (diag - dshift) * dscale * cur[col + r];
+        double diag = model == 0 ? U * (double)__popcll((x >> L) & (x & lowmask)) : 0.0;
+        double hsum = 0.0;
         for (int i = 0; i < nb; ++i) {
             const long long mk = bonds[i];
             const long long bits = x & mk;
-            if (bits != 0 && bits != mk) h += hop * cur[col + t.pos[x ^ mk]];
+            if (bits != 0 && bits != mk) hsum += hop * cur[col + t.pos[x ^ mk]];
+            else if (model == 1 && bits == mk) diag += U;  // n_j n_{j+1} on the bond
         }
+        const double h = (diag - dshift) * dscale * cur[col + r] + hsum;
         const double out = scale * h - (first ? 0.0 : prev_out[e]);
         prev_out[e] = out;
         double2 a = acc[e];
@@ -122,11 +124,11 @@ void launch_cheb_init(const long long *off_u, const long long *sizes, int n_sect
 void launch_cheb_step(const TargetDev &t, int n_sectors, long long total, const double *cur,
                       double *prev_out, double2 *acc, double2 coef, double scale, int first,
                       double diag_scale, double diag_shift, double hop_scale,
-                      const long long *bond_masks, int n_bonds, int L, double U, cudaStream_t s) {
+                      const long long *bond_masks, int n_bonds, int L, double U, int model, cudaStream_t s) {
     const long long blocks = (total + 255) / 256;
     k_cheb_step<<<(int)(blocks < 65536 ? blocks : 65536), 256, 0, s>>>(
         t, n_sectors, total, cur, prev_out, acc, coef, scale, first, diag_scale, diag_shift,
-        hop_scale, bond_masks, n_bonds, L, U);
+        hop_scale, bond_masks, n_bonds, L, U, model);
 }
 
 void launch_scatter_target(const TargetDev &t, const int32_t *cols, const double *wts, int B, int log2B,

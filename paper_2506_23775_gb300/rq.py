@@ -163,7 +163,7 @@ class Context:
     # --- set-up ---------------------------------------------------------
     def setup(self, n_sites: int, pairs, param_of=None, n_params: Optional[int] = None,
               structure: int = 0, J: float = 1.0, U: float = 4.0, t: float = 0.5,
-              periodic: bool = False):
+              periodic: bool = False, model: int = 0):
         pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
         self._pairs = pairs
         if param_of is not None:
@@ -174,17 +174,18 @@ class Context:
             self._param_of = None
             npar = pairs.shape[0]
             pp = None
-        circ = RQCircuit(2 * n_sites, pairs.shape[0], npar, structure,
+        nq = (2 if model == 0 else 1) * n_sites
+        circ = RQCircuit(nq, pairs.shape[0], npar, structure,
                          pairs.ctypes.data_as(C.POINTER(C.c_int32)), pp)
-        tgt = RQTarget(0, n_sites, 1 if periodic else 0, J, U, t)
+        tgt = RQTarget(model, n_sites, 1 if periodic else 0, J, U, t)
         self._check(self._lib.rq_setup_target(self._h, C.byref(tgt), C.byref(circ)))
-        self.n_params, self.n_qubits, self.structure = npar, 2 * n_sites, structure
+        self.n_params, self.n_qubits, self.structure = npar, nq, structure
         return self
 
     def setup_problem(self, prob):
         """Set up from a ``workloads.Problem``."""
         return self.setup(prob.L, prob.pairs, prob.param_of, prob.n_params, prob.structure,
-                          prob.J, prob.U, prob.t, prob.periodic)
+                          prob.J, prob.U, prob.t, prob.periodic, getattr(prob, "model", 0))
 
     def set_gradient_space(self, space: int):
         """0: Riemannian outputs (default); 1: Euclidean gradient and Hessian."""
@@ -347,7 +348,7 @@ class Batch:
         pof = np.ascontiguousarray(prob.param_of, dtype=np.int32)
         circ = RQCircuit(prob.n, pairs.shape[0], prob.n_params, prob.structure,
                          pairs.ctypes.data_as(C.POINTER(C.c_int32)), pof.ctypes.data_as(C.POINTER(C.c_int32)))
-        tgt = RQTarget(0, prob.L, 1 if prob.periodic else 0, prob.J, prob.U, prob.t)
+        tgt = RQTarget(getattr(prob, "model", 0), prob.L, 1 if prob.periodic else 0, prob.J, prob.U, prob.t)
         idx = C.c_int()
         self._check(self._lib.rq_batch_add(self._h, C.byref(tgt), C.byref(circ), C.byref(idx)))
         self.n_params.append(prob.n_params)

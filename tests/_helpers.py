@@ -22,13 +22,13 @@ def assert_close(got, ref, n: int, rtol: float = RTOL, what: str = ""):
 
 
 @functools.lru_cache(maxsize=None)
-def sector_target(L, J, U, t, periodic):
+def sector_target(L, J, U, t, periodic, model_id=0):
     from oracle import model
-    return model.SectorTarget(L, J, U, t, periodic)
+    return model.SectorTarget(L, J, U, t, periodic, model_id)
 
 
 def target_for(prob):
-    return sector_target(prob.L, prob.J, prob.U, prob.t, prob.periodic)
+    return sector_target(prob.L, prob.J, prob.U, prob.t, prob.periodic, getattr(prob, "model", 0))
 
 
 def oracle_eval(prob, cols, Xraw=None, gates=None, chunk=16):

@@ -115,3 +115,39 @@ def test_memory_of_sixteen_qubit_state():
     # 16 qubits is exactly 1 MiB; a dense layer would be 64 GiB.
     assert (1 << 16) * 16 == 1 << 20
     assert 16 * (1 << 16) ** 2 == 64 << 30
+
+
+# ------------------------------------------------------------ spinless chain
+
+@pytest.mark.parametrize("tau", [0.1, 0.77])
+def test_spinless_trotter_gate_is_the_printed_closed_form(tau):
+    # the full two-site Hamiltonian h_loc of the spinless chain (hop + U n n)
+    J, U = 1.0, 2.5
+    np.testing.assert_allclose(w.spinless_gate(tau, J, U), scipy.linalg.expm(-1j * tau * _hloc(J, U)), atol=1e-14)
+
+
+@pytest.mark.parametrize("L,periodic", [(4, False), (5, True), (6, True)])
+def test_spinless_hamiltonian(L, periodic):
+    H = model.hamiltonian_dense(L, 1.0, 2.0, periodic, model=1)
+    np.testing.assert_array_equal(H, H.T)
+    xs = np.arange(1 << L)
+    N = np.diag(np.array([bin(x).count("1") for x in xs], dtype=float))
+    assert np.abs(H @ N - N @ H).max() == 0
+    total = 0
+    for Nn in range(L + 1):
+        Hs, basis = model.hamiltonian_sector(L, 1.0, 2.0, periodic, (Nn,), model=1)
+        np.testing.assert_array_equal(Hs, H[np.ix_(basis, basis)])
+        total += len(basis)
+    assert total == 1 << L
+    # one particle on a periodic ring: hopping band -2J cos(k)
+    if periodic:
+        Hs, _ = model.hamiltonian_sector(L, 1.0, 2.0, True, (1,), model=1)
+        k = 2 * np.pi * np.arange(L) / L
+        np.testing.assert_allclose(np.sort(np.linalg.eigvalsh(Hs)), np.sort(-2 * np.cos(k)), atol=1e-12)
+
+
+def test_spinless_sector_target_equals_dense():
+    H = model.hamiltonian_dense(6, 1.0, 2.0, True, model=1)
+    U = model.target_unitary_dense(H, 0.7)
+    st = model.SectorTarget(6, 1.0, 2.0, 0.7, True, model=1)
+    np.testing.assert_allclose(st.columns(np.arange(64)).T, U, atol=1e-13)

@@ -92,3 +92,16 @@ def test_periodic_wrap_bond_matches_dense():
     assert abs(f - dense.cost(p, Um)) <= 1e-13 * 2 ** p.n
     assert _rel(g, dense.rgrad(p, Um)) < 1e-12
     assert _rel(hv[0], dense.rhess(p, Um, Xt[0], method="cauchy")) < 1e-11
+
+
+@pytest.mark.parametrize("structure,tied,periodic", [(0, False, False), (1, True, True), (0, True, True)])
+def test_spinless_matrix_free_equals_dense(structure, tied, periodic):
+    p = w.make_spinless_problem(6, 5, 0.6, U=2.0, seed=71, structure=structure, tied=tied, periodic=periodic)
+    assert p.n == 6
+    Um = model.target_unitary_dense(model.hamiltonian_dense(6, 1.0, 2.0, periodic, model=1), 0.6)
+    st = model.SectorTarget(6, 1.0, 2.0, 0.6, periodic, model=1)
+    Xraw = w.random_directions(p.n_params, 1, 72)
+    f, g, hv, Xt = sv.cost_grad_hvp(p, st, range(64), Xraw, chunk=64)
+    assert abs(f - dense.cost(p, Um)) <= 1e-13 * 64
+    assert _rel(g, dense.rgrad(p, Um)) < 1e-12
+    assert _rel(hv[0], dense.rhess(p, Um, Xt[0], method="cauchy")) < 1e-11

@@ -17,4 +17,6 @@ from .fermi_hubbard import (  # noqa: F401
     random_directions,
     config_problem,
     batch_problems,
+    make_spinless_problem,
+    spinless_gate,
 )

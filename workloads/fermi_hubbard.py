@@ -132,10 +132,11 @@ class Problem:
     param_of: np.ndarray  # [g] int32
     gates: np.ndarray  # [n_params, 4, 4] complex128
     kinds: List[str] = field(default_factory=list)  # layer kind per gate
+    model: int = 0  # 0 spinful chain (n = 2L), 1 spinless chain (n = L)
 
     @property
     def n(self) -> int:
-        return 2 * self.L
+        return 2 * self.L if self.model == 0 else self.L
 
     @property
     def n_gates(self) -> int:
@@ -186,6 +187,61 @@ def random_directions(n_params: int, k: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return (rng.standard_normal((k, n_params, 4, 4))
             + 1j * rng.standard_normal((k, n_params, 4, 4)))
+
+
+# Spinless chain (paper Eq. slFH_qubit) -----------------------------------------
+
+def spinless_layers(L: int, depth: int, periodic: bool = False):
+    """Even bonds ``E`` = (2k, 2k+1), odd bonds ``O`` = (2k+1, 2k+2) (plus the
+    wrap bond (L-1, 0) of an even periodic chain), alternating ``EOEO...``."""
+    layers = []
+    for i in range(depth):
+        kind = "E" if i % 2 == 0 else "O"
+        start = 0 if kind == "E" else 1
+        pairs = [(s, s + 1) for s in range(start, L - 1, 2)]
+        if periodic and kind == "O" and L % 2 == 0 and L > 2:
+            pairs.append((L - 1, 0))
+        layers.append((kind, pairs))
+    return layers
+
+
+def spinless_times(depth: int, t: float) -> List[float]:
+    """Odd depth 2r+1: r merged Strang steps (outer E layers dt/2, inner E
+    and all O layers dt, dt = t/r); otherwise t split evenly per kind."""
+    if depth % 2 == 1 and depth >= 3:
+        r = (depth - 1) // 2
+        dt = t / r
+        return [dt / 2 if i in (0, depth - 1) else dt for i in range(depth)]
+    kinds = ["E" if i % 2 == 0 else "O" for i in range(depth)]
+    return [t / kinds.count(k) for k in kinds]
+
+
+def spinless_gate(tau: float, J: float, U: float) -> np.ndarray:
+    """The paper's closed form of ``exp(-i tau h_loc)`` (hop + U n n)."""
+    g = trotter_gate("A", tau, J, U)
+    g[3, 3] = np.exp(-1j * U * tau)
+    return g
+
+
+def make_spinless_problem(L: int, depth: int, t: float, U: float = 2.0, J: float = 1.0, seed: int = 0,
+                          structure: int = 0, tied: bool = False, periodic: bool = False,
+                          sigma: float = 1e-2) -> Problem:
+    """Trotter-initialised brickwall for the spinless hard-core-boson chain."""
+    rng = np.random.default_rng(seed)
+    pairs, param_of, gates, kinds = [], [], [], []
+    for (kind, lp), tau in zip(spinless_layers(L, depth, periodic), spinless_times(depth, t)):
+        if tied and lp:
+            gates.append(spinless_gate(tau, J, U) @ _noise(rng, sigma, structure == 1))
+        for p in lp:
+            pairs.append(p)
+            kinds.append(kind)
+            if not tied:
+                gates.append(spinless_gate(tau, J, U) @ _noise(rng, sigma, structure == 1))
+            param_of.append(len(gates) - 1)
+    return Problem(L=L, depth=depth, t=t, J=J, U=U, periodic=periodic, structure=structure,
+                   pairs=np.asarray(pairs, dtype=np.int32).reshape(-1, 2),
+                   param_of=np.asarray(param_of, dtype=np.int32),
+                   gates=np.asarray(gates, dtype=np.complex128).reshape(-1, 4, 4), kinds=kinds, model=1)
 
 
 # Named workloads ------------------------------------------------------------
