@@ -290,6 +290,47 @@ def run_ours(args):
                 "workload": "256 problems: n in {8,10,12}, depth in {3,5,7,9}, t~U[0.1,1], U~U[2,8], "
                             "general gates, f + grad + 1 HVP each, full basis sums (seed 301)"}
 
+    def measure_served():
+        """Continuous batching against one-at-a-time service of the same requests:
+        cost/grad/HVP requests for n in {10, 12, 14, 16} (n = 16: parity-gate cost
+        over the full basis), depths 3-11, t ~ U[0.1, 1], U = 4."""
+        from paper_2506_23775_gb300 import serve
+        rng = np.random.default_rng(501)
+        probs, kinds = [], []
+        for i in range(40):
+            n = int(rng.choice([10, 12, 14, 16], p=[0.35, 0.35, 0.2, 0.1]))
+            L = n // 2
+            if n == 16:
+                depth, kind, structure = int(rng.integers(3, 8)), "cost", 1
+            elif n == 14:
+                depth, kind, structure = int(rng.integers(3, 6)), str(rng.choice(["cost", "grad"])), 0
+            else:
+                depth, kind, structure = int(rng.integers(3, 12)), str(rng.choice(["cost", "grad", "hvp"])), 0
+            t = round(float(rng.uniform(0.1, 1.0)), 1)   # a few distinct targets, so contexts are reused
+            probs.append(w.make_problem(L, depth, t, U=4.0, seed=5000 + i, structure=structure))
+            kinds.append(kind)
+        # plain: one request at a time, all available at once
+        srv = serve.Server(local, max_inflight=1, tile=128)
+        reqs = serve.poisson_stream(probs, kinds, rate_hz=1e9, seed=502)
+        plain = srv.run(reqs, realtime=False)
+        srv.close()
+        capacity = plain["evals_per_s"]
+        # served: Poisson arrivals at 80 % of the plain capacity, up to 8 in flight
+        srv = serve.Server(local, max_inflight=8, tile=128)
+        reqs = serve.poisson_stream(probs, kinds, rate_hz=0.8 * capacity, seed=503)
+        served = srv.run(reqs, realtime=True)
+        srv.close()
+        # burst: every request available at once, up to 8 in flight
+        srv = serve.Server(local, max_inflight=8, tile=128)
+        reqs = serve.poisson_stream(probs, kinds, rate_hz=1e9, seed=504)
+        burst = srv.run(reqs, realtime=False)
+        srv.close()
+        return {"requests": len(probs), "unit": "requests/s",
+                "plain": plain, "served_poisson_80pct": served, "served_burst": burst,
+                "throughput_ratio_burst_vs_plain": burst["evals_per_s"] / plain["evals_per_s"],
+                "workload": "40 requests: n in {10,12,14,16} (p = .35/.35/.2/.1), depth 3-11 (n=14: 3-5, "
+                            "n=16: 3-7, parity-gate cost), cost/grad/hvp, t in {0.1..1.0}, U=4, full basis sums"}
+
     gen = measure(0, args.steps, args.warmup, args.tile)
     par = None
     if not args.general_only:
@@ -300,7 +341,8 @@ def run_ours(args):
         if not args.general_only:
             df_par = measure(1, args.steps, args.warmup, args.tile, arith=1)
 
-    batched = measure_batched() if (args.batched and world == 1) else None
+    batched = measure_batched() if (not args.no_batched and world == 1) else None
+    served = measure_served() if (not args.no_served and world == 1) else None
 
     if rank != 0:
         if world > 1:
@@ -363,6 +405,8 @@ def run_ours(args):
                                       "gpu_launches": df_par["launches"], "clocks": df_par["clocks"]}
     if batched is not None:
         line["batched"] = batched
+    if served is not None:
+        line["served"] = served
     if world == 1 and not args.no_cpu:
         rates, cores, ncols = cpu_oracle_rate(per_worker=1)
         line["cpu_baseline"] = {"value": rates[0], "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -407,7 +451,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--tile", type=int, default=0, help="columns per tile (power of two; 0 = automatic)")
     ap.add_argument("--general-only", action="store_true", help="skip the parity-gate measurement")
-    ap.add_argument("--batched", action="store_true", help="also time 256 uneven problems batched vs plain")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-problem batched-vs-plain measurement")
+    ap.add_argument("--no-served", action="store_true", help="skip the continuous-batching request stream")
     ap.add_argument("--no-df64", action="store_true", help="skip the double-float arithmetic measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--sites", type=int, default=8, help="chain sites (n = 2 * sites); profiling cases only")
