@@ -179,3 +179,22 @@ def test_polar_retraction(rng):
         P = Q[i].conj().T @ A[i]  # Hermitian positive definite
         np.testing.assert_allclose(P, P.conj().T, atol=1e-12)
         assert np.linalg.eigvalsh(0.5 * (P + P.conj().T)).min() > 0
+
+
+def test_fourth_order_trotter_initialisation():
+    # 21 layers; the times of each kind add up to t; the noise-free circuit's
+    # error ||C - U||_F^2 = 2 * 2^n + 2 f falls like t^10 (local error O(t^5))
+    taus = w.trotter4_times(0.3)
+    kinds = w.layer_pattern(21)
+    assert len(taus) == 21
+    for k in "ABC":
+        np.testing.assert_allclose(sum(t for t, kk in zip(taus, kinds) if kk == k), 0.3, rtol=1e-14)
+    errs = []
+    for t in (0.2, 0.1):
+        p, Um = _setup(L=3, depth=21, t=t, sigma=0.0)
+        p = w.make_problem(3, 21, t, sigma=0.0, order=4)
+        Um = model.target_unitary_dense(model.hamiltonian_dense(3, 1.0, 4.0), t)
+        errs.append(2 * 2 ** p.n + 2 * dense.cost(p, Um))
+        p2 = w.make_problem(3, 5, t, sigma=0.0)
+        assert errs[-1] < 2 * 2 ** p.n + 2 * dense.cost(p2, Um)   # better than 2nd order
+    assert 2 ** 9 < errs[0] / errs[1] < 2 ** 11

@@ -11,6 +11,7 @@ from .fermi_hubbard import (  # noqa: F401
     brickwall_layers,
     layer_pattern,
     trotter_times,
+    trotter4_times,
     trotter_gate,
     parity_mask,
     make_problem,

@@ -92,6 +92,24 @@ def trotter_times(depth: int, t: float) -> List[float]:
     return [t / counts[k] for k in kinds]
 
 
+def trotter4_times(t: float) -> List[float]:
+    """21 layer times of a 4th-order Suzuki step for the 3-term split A + B + C.
+
+    ``S4(t) = S2(p t)^2 S2((1 - 4p) t) S2(p t)^2`` with ``p = 1 / (4 - 4^(1/3))``
+    and the nested Strang step ``S2(s) = A(s/2) B(s/2) C(s) B(s/2) A(s/2)``;
+    adjacent ``A`` factors of consecutive steps merge, leaving
+    ``5 * 4 + 1 = 21`` layers ``ABCB...A``.
+    """
+    p = 1.0 / (4.0 - 4.0 ** (1.0 / 3.0))
+    steps = [p, p, 1.0 - 4.0 * p, p, p]
+    out = [steps[0] * t / 2]
+    for k, sk in enumerate(steps):
+        out += [sk * t / 2, sk * t, sk * t / 2]
+        nxt = steps[k + 1] * t / 2 if k + 1 < len(steps) else 0.0
+        out.append(sk * t / 2 + nxt)
+    return out
+
+
 def trotter_gate(kind: str, tau: float, J: float, U: float) -> np.ndarray:
     """Closed-form ``exp(-i tau h)`` for a hopping (A/B) or on-site (C) pair."""
     g = np.zeros((4, 4), dtype=np.complex128)
@@ -149,15 +167,22 @@ class Problem:
 
 def make_problem(L: int, depth: int, t: float, U: float = 4.0, J: float = 1.0,
                  seed: int = 0, structure: int = 0, tied: bool = False,
-                 periodic: bool = False, sigma: float = 1e-2) -> Problem:
+                 periodic: bool = False, sigma: float = 1e-2, order: int = 2) -> Problem:
     """Trotter-initialised brickwall for the spinful chain with seeded noise.
 
     ``tied``: one parameter gate per layer (translation-invariant ansatz,
     paper Sec. "Brick wall circuit layout"); otherwise one per gate.
+    ``order = 4`` (with ``depth = 21``): the 4th-order Suzuki initialisation
+    the paper uses for its convergence comparison.
     """
     rng = np.random.default_rng(seed)
     layers = brickwall_layers(L, depth, periodic)
-    taus = trotter_times(depth, t)
+    if order == 4:
+        if depth != 21:
+            raise ValueError("the 4th-order initialisation has 21 layers")
+        taus = trotter4_times(t)
+    else:
+        taus = trotter_times(depth, t)
     pairs, param_of, gates, kinds = [], [], [], []
     for li, ((kind, lp), tau) in enumerate(zip(layers, taus)):
         if tied and lp:
