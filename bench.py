@@ -291,45 +291,40 @@ def run_ours(args):
                             "general gates, f + grad + 1 HVP each, full basis sums (seed 301)"}
 
     def measure_served():
-        """Continuous batching against one-at-a-time service of the same requests:
-        cost/grad/HVP requests for n in {10, 12, 14, 16} (n = 16: parity-gate cost
-        over the full basis), depths 3-11, t ~ U[0.1, 1], U = 4."""
+        """Continuous batching against one-at-a-time service of the same requests.
+
+        48 cost / grad / HVP requests over 6 problems (an optimiser keeps asking
+        about the same circuits at new gates): n = 10 (depth 11), 12 (depths 5
+        and 9), 14 (depth 5), 16 (depth 5, parity gates: cost only, full basis),
+        and 10 (depth 7); t in [0.1, 1], U = 4."""
         from paper_2506_23775_gb300 import serve
+        specs = [(5, 11, 0.3, 0, ("cost", "grad", "hvp")), (6, 5, 0.6, 0, ("cost", "grad", "hvp")),
+                 (6, 9, 0.9, 0, ("cost", "grad", "hvp")), (7, 5, 0.5, 0, ("cost", "grad")),
+                 (8, 5, 0.5, 1, ("cost",)), (5, 7, 0.2, 0, ("cost", "grad", "hvp"))]
         rng = np.random.default_rng(501)
         probs, kinds = [], []
-        for i in range(40):
-            n = int(rng.choice([10, 12, 14, 16], p=[0.35, 0.35, 0.2, 0.1]))
-            L = n // 2
-            if n == 16:
-                depth, kind, structure = int(rng.integers(3, 8)), "cost", 1
-            elif n == 14:
-                depth, kind, structure = int(rng.integers(3, 6)), str(rng.choice(["cost", "grad"])), 0
-            else:
-                depth, kind, structure = int(rng.integers(3, 12)), str(rng.choice(["cost", "grad", "hvp"])), 0
-            t = round(float(rng.uniform(0.1, 1.0)), 1)   # a few distinct targets, so contexts are reused
+        for i in range(48):
+            L, depth, t, structure, ks = specs[int(rng.integers(len(specs)))]
             probs.append(w.make_problem(L, depth, t, U=4.0, seed=5000 + i, structure=structure))
-            kinds.append(kind)
-        # plain: one request at a time, all available at once
-        srv = serve.Server(local, max_inflight=1, tile=128)
-        reqs = serve.poisson_stream(probs, kinds, rate_hz=1e9, seed=502)
-        plain = srv.run(reqs, realtime=False)
+            kinds.append(str(rng.choice(ks)))
+        out = {}
+        # plain: one request at a time, all available at once, one context per problem
+        srv = serve.Server(local, max_inflight=1, tile=128, contexts_per_problem=1, setup_workers=1)
+        srv.run(serve.poisson_stream(probs[:6], kinds[:6], rate_hz=1e9, seed=7), realtime=False)  # warm-up
+        out["plain"] = srv.run(serve.poisson_stream(probs, kinds, rate_hz=1e9, seed=502), realtime=False)
         srv.close()
-        capacity = plain["evals_per_s"]
-        # served: Poisson arrivals at 80 % of the plain capacity, up to 8 in flight
-        srv = serve.Server(local, max_inflight=8, tile=128)
-        reqs = serve.poisson_stream(probs, kinds, rate_hz=0.8 * capacity, seed=503)
-        served = srv.run(reqs, realtime=True)
-        srv.close()
-        # burst: every request available at once, up to 8 in flight
-        srv = serve.Server(local, max_inflight=8, tile=128)
-        reqs = serve.poisson_stream(probs, kinds, rate_hz=1e9, seed=504)
-        burst = srv.run(reqs, realtime=False)
-        srv.close()
-        return {"requests": len(probs), "unit": "requests/s",
-                "plain": plain, "served_poisson_80pct": served, "served_burst": burst,
-                "throughput_ratio_burst_vs_plain": burst["evals_per_s"] / plain["evals_per_s"],
-                "workload": "40 requests: n in {10,12,14,16} (p = .35/.35/.2/.1), depth 3-11 (n=14: 3-5, "
-                            "n=16: 3-7, parity-gate cost), cost/grad/hvp, t in {0.1..1.0}, U=4, full basis sums"}
+        capacity = out["plain"]["evals_per_s"]
+        for name, rate in (("served_burst", 1e9), ("served_poisson_80pct", 0.8 * capacity)):
+            srv = serve.Server(local, max_inflight=8, tile=128, contexts_per_problem=2, setup_workers=2)
+            srv.run(serve.poisson_stream(probs[:6], kinds[:6], rate_hz=1e9, seed=7), realtime=False)
+            out[name] = srv.run(serve.poisson_stream(probs, kinds, rate_hz=rate, seed=503),
+                                realtime=rate < 1e8)
+            srv.close()
+        out.update({"requests": len(probs), "unit": "requests/s",
+                    "throughput_ratio_burst_vs_plain": out["served_burst"]["evals_per_s"] / capacity,
+                    "workload": "48 requests over 6 problems (n = 10, 12, 12, 14, 16 parity cost, 10), "
+                                "cost/grad/hvp, full basis sums; contexts warmed on 6 requests first"})
+        return out
 
     gen = measure(0, args.steps, args.warmup, args.tile)
     par = None

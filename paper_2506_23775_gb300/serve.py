@@ -7,7 +7,8 @@ its evaluation at once on that request's own CUDA stream -- so requests that
 arrive while others are on the GPU run concurrently with them -- and returns
 each result when its completion event fires.  Target blocks and workspaces
 stay on the device between requests for the same problem (a context cache),
-so repeated requests skip the set-up.
+so repeated requests skip the set-up; new contexts are built by host worker
+threads while the loop keeps admitting and collecting work.
 
 Every evaluation runs the library's kernels in the same order as the same
 request evaluated alone on a context with the same tile size, so a result in
@@ -68,11 +69,17 @@ class Server:
 
     ``memory_budget``: bytes of device memory the server may hold;
     ``max_inflight``: evaluations on the GPU at once; ``tile``: columns per
-    tile of every context (a power of two; smaller tiles lower the footprint).
+    tile of every context (a power of two; smaller tiles lower the footprint);
+    ``contexts_per_problem``: contexts one problem may hold at once (several
+    requests for the same problem then run concurrently); ``setup_workers``:
+    host threads that build new contexts (target blocks) while the loop keeps
+    admitting and collecting work.
     """
 
     def __init__(self, device: int = 0, memory_budget: Optional[int] = None, max_inflight: int = 8,
-                 tile: int = 128):
+                 tile: int = 128, contexts_per_problem: int = 2, setup_workers: int = 2):
+        import concurrent.futures as cf
+
         import torch
         from . import rq
         self.torch, self.rq = torch, rq
@@ -84,33 +91,51 @@ class Server:
         self.budget = memory_budget
         self.max_inflight = max_inflight
         self.tile = tile
-        self.cache: "collections.OrderedDict[tuple, _Slot]" = collections.OrderedDict()
+        self.per_problem = contexts_per_problem
+        self.slots: Dict[tuple, List[_Slot]] = collections.defaultdict(list)
+        self.building: Dict[tuple, list] = collections.defaultdict(list)   # futures of contexts being set up
         self.held = 0
         self.stats = collections.Counter()
+        self.pool = cf.ThreadPoolExecutor(max_workers=setup_workers)
 
     # -- contexts ----------------------------------------------------------
     def _evict_idle(self, need: int) -> bool:
-        for key in list(self.cache.keys()):
+        idle = sorted((s.last_used, id(s), s) for lst in self.slots.values() for s in lst if not s.busy)
+        for _, _, s in idle:
             if self.held + need <= self.budget:
-                return True
-            s = self.cache[key]
-            if not s.busy:
-                s.ctx.close()
-                self.held -= s.nbytes
-                del self.cache[key]
-                self.stats["evicted"] += 1
+                break
+            s.ctx.close()
+            self.held -= s.nbytes
+            self.slots[s.key].remove(s)
+            self.stats["evicted"] += 1
         return self.held + need <= self.budget
+
+    def _build(self, p, key, tile, need):
+        self.torch.cuda.set_device(self.dev)
+        stream = self.torch.cuda.Stream(device=self.dev)
+        ctx = self.rq.Context(self.device, stream=stream.cuda_stream).setup_problem(p)
+        ctx.set_tile(tile, 1)
+        return _Slot(ctx, stream, key, tile, need)
+
+    def _harvest_builds(self):
+        for key, futs in self.building.items():
+            done = [fu for fu in futs if fu.done()]
+            for fu in done:
+                futs.remove(fu)
+                self.slots[key].append(fu.result())   # re-raises a failed set-up
+                self.stats["setups"] += 1
 
     def _slot_for(self, req: Request) -> Optional[_Slot]:
         p = req.problem
         key = problem_key(p)
-        s = self.cache.get(key)
-        if s is not None:
-            if s.busy:
-                return None                   # one evaluation per context at a time
-            self.cache.move_to_end(key)
-            self.stats["reused"] += 1
-            return s
+        for s in self.slots[key]:
+            if not s.busy:
+                self.stats["reused"] += 1
+                return s
+        if len(self.slots[key]) + len(self.building[key]) >= self.per_problem:
+            return None                       # wait for one of this problem's contexts
+        if self.building[key]:
+            return None                       # one set-up at a time per problem
         tile = min(self.tile, 1 << p.n)
         k = 0 if req.dirs is None else req.dirs.shape[0]
         need = footprint_bytes(p, tile, max(k, 1))
@@ -118,14 +143,9 @@ class Server:
             raise MemoryError(f"request {req.rid} needs {need} bytes, the budget is {self.budget}")
         if not self._evict_idle(need):
             return None
-        stream = self.torch.cuda.Stream(device=self.dev)
-        ctx = self.rq.Context(self.device, stream=stream.cuda_stream).setup_problem(p)
-        ctx.set_tile(tile, 1)
-        s = _Slot(ctx, stream, key, tile, need)
-        self.cache[key] = s
         self.held += need
-        self.stats["setups"] += 1
-        return s
+        self.building[key].append(self.pool.submit(self._build, p, key, tile, need))
+        return None
 
     # -- one evaluation, queued on the slot's stream ------------------------
     def _launch(self, req: Request, s: _Slot):
@@ -161,12 +181,13 @@ class Server:
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0
         waiting: List[Request] = []
-        while pending or waiting or inflight:
+        while pending or waiting or inflight or any(self.building.values()):
             t = now()
             while pending and (not realtime or pending[0].arrival <= t):
                 waiting.append(pending.popleft())
+            self._harvest_builds()
             # admit as slots and memory allow (first come, first served; a
-            # request whose context is busy does not block later ones)
+            # request whose problem has no free context does not block others)
             still = []
             for req in waiting:
                 if len(inflight) >= self.max_inflight:
@@ -196,7 +217,7 @@ class Server:
                 else:
                     rest.append(item)
             inflight = rest
-            if inflight or waiting or pending:
+            if inflight or waiting or pending or any(self.building.values()):
                 time.sleep(0.0005)
         wall = now()
         lat = np.array([r.latency for r in requests])
@@ -205,9 +226,12 @@ class Server:
                 "setups": self.stats["setups"], "reused": self.stats["reused"], "evicted": self.stats["evicted"]}
 
     def close(self):
-        for s in self.cache.values():
-            s.ctx.close()
-        self.cache.clear()
+        self.pool.shutdown(wait=True)
+        self._harvest_builds()
+        for lst in self.slots.values():
+            for s in lst:
+                s.ctx.close()
+        self.slots.clear()
         self.held = 0
 
 

@@ -33,7 +33,7 @@ def _stream(serve):
 def test_results_in_the_mix_equal_results_alone(mods):
     rq, serve = mods
     reqs = _stream(serve)
-    srv = serve.Server(0, memory_budget=8 << 30, max_inflight=4, tile=64)
+    srv = serve.Server(0, memory_budget=8 << 30, max_inflight=4, tile=64, contexts_per_problem=2)
     stats = srv.run(reqs)
     srv.close()
     assert stats["requests"] == len(reqs) and stats["reused"] > 0
