@@ -326,6 +326,29 @@ def run_ours(args):
                                 "cost/grad/hvp, full basis sums; contexts warmed on 6 requests first"})
         return out
 
+    def measure_sweeps():
+        """Gradient time per basis summand (the paper's Fig. matchgate_gradient):
+        spinful chains with 5 layers for n = 6..16, and n = 10 for 1..21 layers;
+        FP64, general gates.  Each point: one warm-up gradient, then the median
+        of three timed gradients over min(2^n, 4096) columns, divided by the
+        number of columns."""
+        def point(L, depth):
+            prob = w.make_problem(L, depth, 0.5, seed=900 + L * 31 + depth)
+            ctx = rq.Context(local).setup_problem(prob)
+            ncols = min(1 << prob.n, 4096)
+            ctx.set_columns(0, ncols)
+            ctx.grad(prob.gates)
+            ts = []
+            for _ in range(3):
+                t0 = time.perf_counter()
+                ctx.grad(prob.gates)
+                ts.append(time.perf_counter() - t0)
+            ctx.close()
+            return {"n": prob.n, "layers": depth, "gates": prob.n_gates, "columns": ncols,
+                    "s_per_summand": float(np.median(ts)) / ncols}
+        return {"vs_qubits_5_layers": [point(L, 5) for L in (3, 4, 5, 6, 7, 8)],
+                "vs_layers_10_qubits": [point(5, d) for d in (1, 3, 5, 7, 9, 11, 15, 21)]}
+
     gen = measure(0, args.steps, args.warmup, args.tile)
     par = None
     if not args.general_only:
@@ -338,6 +361,7 @@ def run_ours(args):
 
     batched = measure_batched() if (not args.no_batched and world == 1) else None
     served = measure_served() if (not args.no_served and world == 1) else None
+    sweeps = measure_sweeps() if (args.sweeps and world == 1) else None
 
     if rank != 0:
         if world > 1:
@@ -402,6 +426,8 @@ def run_ours(args):
         line["batched"] = batched
     if served is not None:
         line["served"] = served
+    if sweeps is not None:
+        line["sweeps"] = sweeps
     if world == 1 and not args.no_cpu:
         rates, cores, ncols = cpu_oracle_rate(per_worker=1)
         line["cpu_baseline"] = {"value": rates[0], "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -448,6 +474,7 @@ def main():
     ap.add_argument("--general-only", action="store_true", help="skip the parity-gate measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-problem batched-vs-plain measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the continuous-batching request stream")
+    ap.add_argument("--sweeps", action="store_true", help="also time the gradient per summand vs n and layers")
     ap.add_argument("--no-df64", action="store_true", help="skip the double-float arithmetic measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--sites", type=int, default=8, help="chain sites (n = 2 * sites); profiling cases only")
