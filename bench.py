@@ -314,6 +314,11 @@ def run_ours(args):
         out["plain"] = srv.run(serve.poisson_stream(probs, kinds, rate_hz=1e9, seed=502), realtime=False)
         srv.close()
         capacity = out["plain"]["evals_per_s"]
+        srv = serve.Server(local, max_inflight=1, tile=128, contexts_per_problem=1, setup_workers=1)
+        srv.run(serve.poisson_stream(probs[:6], kinds[:6], rate_hz=1e9, seed=7), realtime=False)
+        out["plain_poisson_80pct"] = srv.run(serve.poisson_stream(probs, kinds, rate_hz=0.8 * capacity, seed=503),
+                                             realtime=True)
+        srv.close()
         for name, rate in (("served_burst", 1e9), ("served_poisson_80pct", 0.8 * capacity)):
             srv = serve.Server(local, max_inflight=8, tile=128, contexts_per_problem=2, setup_workers=2)
             srv.run(serve.poisson_stream(probs[:6], kinds[:6], rate_hz=1e9, seed=7), realtime=False)

@@ -458,6 +458,142 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_dir_df(const BwdArgs a) {
     block_reduce_store(E, a.part + (long long)blockIdx.x * kEnvDoubles);
 }
 
+// ------------------------------------------- two threads per item (4-amp) --
+//
+// The environment accumulators dominate the registers of the df64 backward
+// kernels (16 complex df64 sums = 64 floats).  For gates whose items have four
+// amplitudes, two adjacent lanes share an item: lane h accumulates the
+// environment rows {2h, 2h+1} and writes the updated amplitudes {2h, 2h+1}.
+// Half the accumulators per thread lets two CTAs share an SM (twice the
+// resident warps to hide memory latency); the pair's loads coalesce into the
+// same transactions.
+
+// Block sum of the 8 entries each lane holds: even lanes carry rows {0, 1}
+// (entries 0..7), odd lanes rows {2, 3} (entries 8..15).
+__device__ __forceinline__ void block_reduce_store_half(const CAcc (&acc)[8], double *out) {
+    __shared__ double red[kThreads / 32][kEnvDoubles];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const double2 v = to_double(acc[i]);
+        double vx = v.x, vy = v.y;
+#pragma unroll
+        for (int o = 16; o > 1; o >>= 1) {  // sums over lanes of the same parity
+            vx += __shfl_xor_sync(0xffffffffu, vx, o);
+            vy += __shfl_xor_sync(0xffffffffu, vy, o);
+        }
+        if (lane < 2) {
+            red[warp][2 * (lane * 8 + i)] = vx;
+            red[warp][2 * (lane * 8 + i) + 1] = vy;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kEnvDoubles) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) s += red[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+// Lane h of a pair owns rows i = 2h + u, u = 0, 1.  Every register index is
+// static; the lane's rows are picked with selects (no divergence, no local
+// memory).  For a parity gate row i couples the columns of its block:
+// {0, 3} if i is 0 or 3, else {1, 2}; "even" below is that test.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 2) k_bwd_dir_df2(const BwdArgs a) {
+    __shared__ float4 sg[16];
+    __shared__ float4 sx[16];
+    const float4 *gate = reinterpret_cast<const float4 *>(a.gate);
+    const float4 *dir = reinterpret_cast<const float4 *>(a.dir);
+    if (threadIdx.x < 16) {
+        sg[threadIdx.x] = gate[threadIdx.x];
+        sx[threadIdx.x] = dir[threadIdx.x];
+    }
+    __syncthreads();
+    const float4 *lam = reinterpret_cast<const float4 *>(a.lam);
+    float4 *dlam = reinterpret_cast<float4 *>(a.dlam);
+    const float4 *psi = reinterpret_cast<const float4 *>(a.psi);
+    const float4 *dpsi = reinterpret_cast<const float4 *>(a.dpsi);
+    CAcc E[8];  // general: E[u*4 + c]; parity: E[u*4 + k], k = 0, 1 the block columns
+#pragma unroll
+    for (int i = 0; i < 8; ++i) E[i] = czero();
+    const int h = threadIdx.x & 1;
+    const long long Bm = (1LL << a.log2B) - 1;
+    const long long stride = ((long long)gridDim.x * blockDim.x) >> 1;
+    const long long start = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 1;
+    for (long long it = start; it < a.n_items; it += stride) {
+        const long long b = it & Bm, r = it >> a.log2B;
+        long long off[4];
+        offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
+        float4 l[4], dl[4], p[4], dp[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            l[c] = __ldg(&lam[off[c]]);
+            dl[c] = dlam[off[c]];
+            p[c] = __ldg(&psi[off[c]]);
+            dp[c] = __ldg(&dpsi[off[c]]);
+        }
+        __syncwarp();  // both lanes of the pair have read dlam before either writes it
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float4 li = h ? l[2 + u] : l[u];
+            const float4 dli = h ? dl[2 + u] : dl[u];
+            if (MODE == kGeneral) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    cmacc(E[u * 4 + c], dli, p[c]);
+                    cmacc(E[u * 4 + c], li, dp[c]);
+                }
+            } else {
+                const bool even = (h == 0) == (u == 0);
+                const float4 pa = even ? p[0] : p[1], pb = even ? p[3] : p[2];
+                const float4 qa = even ? dp[0] : dp[1], qb = even ? dp[3] : dp[2];
+                cmacc(E[u * 4 + 0], dli, pa);
+                cmacc(E[u * 4 + 0], li, qa);
+                cmacc(E[u * 4 + 1], dli, pb);
+                cmacc(E[u * 4 + 1], li, qb);
+            }
+        }
+        if (a.update) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int i = 2 * h + u;
+                CAcc q;
+                if (MODE == kGeneral) {
+                    csetc(q, sg[0 * 4 + i], dl[0]);
+#pragma unroll
+                    for (int c = 1; c < 4; ++c) cmacc(q, sg[c * 4 + i], dl[c]);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) cmacc(q, sx[c * 4 + i], l[c]);
+                } else {
+                    const bool even = (h == 0) == (u == 0);
+                    const int c0 = even ? 0 : 1, c1 = even ? 3 : 2;
+                    csetc(q, sg[c0 * 4 + i], even ? dl[0] : dl[1]);
+                    cmacc(q, sg[c1 * 4 + i], even ? dl[3] : dl[2]);
+                    cmacc(q, sx[c0 * 4 + i], even ? l[0] : l[1]);
+                    cmacc(q, sx[c1 * 4 + i], even ? l[3] : l[2]);
+                }
+                const long long oi = h ? off[2 + u] : off[u];
+                dlam[oi] = fin(q);
+            }
+        }
+    }
+    if (MODE != kGeneral) {
+        // spread the block columns to their 4x4 positions: row 2h+u, columns c0, c1
+#pragma unroll
+        for (int u = 1; u >= 0; --u) {
+            const bool even = (h == 0) == (u == 0);
+            const CAcc k0 = E[u * 4 + 0], k1 = E[u * 4 + 1];
+            E[u * 4 + 0] = even ? k0 : czero();
+            E[u * 4 + 1] = even ? czero() : k0;
+            E[u * 4 + 2] = even ? czero() : k1;
+            E[u * 4 + 3] = even ? k1 : czero();
+        }
+    }
+    block_reduce_store_half(E, a.part + (long long)blockIdx.x * kEnvDoubles);
+}
+
 // psi_0 = |j_b> (the tile is zeroed before): df64 one = (1, 0, 0, 0).
 __global__ void k_init_unit_df(float4 *psi0, const int32_t *cols, int B, int log2B, long long mask) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -530,8 +666,8 @@ void launch_bwd_base_df64(const BwdArgs &a, int grid, cudaStream_t s) {
 
 void launch_bwd_dir_df64(const BwdArgs &a, int grid, cudaStream_t s) {
     switch (a.geo.mode) {
-        case kGeneral: k_bwd_dir_df<kGeneral><<<grid, kThreads, 0, s>>>(a); break;
-        case kParity4: k_bwd_dir_df<kParity4><<<grid, kThreads, 0, s>>>(a); break;
+        case kGeneral: k_bwd_dir_df2<kGeneral><<<grid, kThreads, 0, s>>>(a); break;
+        case kParity4: k_bwd_dir_df2<kParity4><<<grid, kThreads, 0, s>>>(a); break;
         default: k_bwd_dir_df<kParity2><<<grid, kThreads, 0, s>>>(a); break;
     }
 }

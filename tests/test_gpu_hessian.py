@@ -70,3 +70,14 @@ def test_full_hessian_trust_region_equals_hvp_trust_region(rq, structure):
         assert s1.n_inner == s2.n_inner and s1.tcg_exit == s2.tcg_exit and s1.accepted == s2.accepted
         assert abs(s1.rho - s2.rho) <= 1e-6 * max(1.0, abs(s1.rho))
         assert np.abs(G1 - G2).max() <= 1e-10
+
+
+def test_hessian_with_translation_representatives(rq):
+    prob = w.make_problem(4, 5, 0.4, seed=95, tied=True, periodic=True, structure=1)
+    ctx = rq.Context(0).setup_problem(prob)
+    f, eg, H = ctx.hessian(prob.gates)
+    ctx.set_translation(2)
+    f2, eg2, H2 = ctx.hessian(prob.gates)
+    assert abs(f2 - f) <= 1e-12 * abs(f)
+    assert_close(eg2, eg, 8)
+    assert_close(H2, H, 8, what="H with orbit representatives")
