@@ -534,7 +534,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_dir_df2(const BwdArgs a) {
             p[c] = __ldg(&psi[off[c]]);
             dp[c] = __ldg(&dpsi[off[c]]);
         }
-        __syncwarp();  // both lanes of the pair have read dlam before either writes it
+        // both lanes of the pair have read dlam before either writes it; the mask
+        // names only the pair, whose lanes always run the same iterations
+        __syncwarp(0x3u << (threadIdx.x & 30));
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const float4 li = h ? l[2 + u] : l[u];
@@ -581,6 +583,85 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_dir_df2(const BwdArgs a) {
     }
     if (MODE != kGeneral) {
         // spread the block columns to their 4x4 positions: row 2h+u, columns c0, c1
+#pragma unroll
+        for (int u = 1; u >= 0; --u) {
+            const bool even = (h == 0) == (u == 0);
+            const CAcc k0 = E[u * 4 + 0], k1 = E[u * 4 + 1];
+            E[u * 4 + 0] = even ? k0 : czero();
+            E[u * 4 + 1] = even ? czero() : k0;
+            E[u * 4 + 2] = even ? czero() : k1;
+            E[u * 4 + 3] = even ? k1 : czero();
+        }
+    }
+    block_reduce_store_half(E, a.part + (long long)blockIdx.x * kEnvDoubles);
+}
+
+// Base step with two lanes per item (same row split as k_bwd_dir_df2).
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 2) k_bwd_base_df2(const BwdArgs a) {
+    __shared__ float4 sg[16];
+    const float4 *gate = reinterpret_cast<const float4 *>(a.gate);
+    if (threadIdx.x < 16) sg[threadIdx.x] = gate[threadIdx.x];
+    __syncthreads();
+    float4 *lam = reinterpret_cast<float4 *>(a.lam);
+    const float4 *psi = reinterpret_cast<const float4 *>(a.psi);
+    const int accumulate = a.accumulate;
+    CAcc E[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) E[i] = czero();
+    const int h = threadIdx.x & 1;
+    const long long Bm = (1LL << a.log2B) - 1;
+    const long long stride = ((long long)gridDim.x * blockDim.x) >> 1;
+    const long long start = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 1;
+    for (long long it = start; it < a.n_items; it += stride) {
+        const long long b = it & Bm, r = it >> a.log2B;
+        long long off[4];
+        offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
+        float4 l[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) l[c] = lam[off[c]];
+        // both lanes of the pair have read lambda before either writes it; the
+        // mask names only the pair, whose lanes always run the same iterations
+        __syncwarp(0x3u << (threadIdx.x & 30));
+        if (accumulate) {
+            float4 p[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) p[c] = __ldg(&psi[off[c]]);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const float4 li = h ? l[2 + u] : l[u];
+                if (MODE == kGeneral) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) cmacc(E[u * 4 + c], li, p[c]);
+                } else {
+                    const bool even = (h == 0) == (u == 0);
+                    cmacc(E[u * 4 + 0], li, even ? p[0] : p[1]);
+                    cmacc(E[u * 4 + 1], li, even ? p[3] : p[2]);
+                }
+            }
+        }
+        if (a.update) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int i = 2 * h + u;
+                CAcc q;
+                if (MODE == kGeneral) {
+                    csetc(q, sg[0 * 4 + i], l[0]);
+#pragma unroll
+                    for (int c = 1; c < 4; ++c) cmacc(q, sg[c * 4 + i], l[c]);
+                } else {
+                    const bool even = (h == 0) == (u == 0);
+                    const int c0 = even ? 0 : 1, c1 = even ? 3 : 2;
+                    csetc(q, sg[c0 * 4 + i], even ? l[0] : l[1]);
+                    cmacc(q, sg[c1 * 4 + i], even ? l[3] : l[2]);
+                }
+                const long long oi = h ? off[2 + u] : off[u];
+                lam[oi] = fin(q);
+            }
+        }
+    }
+    if (!accumulate) return;
+    if (MODE != kGeneral) {
 #pragma unroll
         for (int u = 1; u >= 0; --u) {
             const bool even = (h == 0) == (u == 0);
@@ -658,8 +739,8 @@ void launch_fwd_df64(const FwdArgs &a, int grid, cudaStream_t s) {
 
 void launch_bwd_base_df64(const BwdArgs &a, int grid, cudaStream_t s) {
     switch (a.geo.mode) {
-        case kGeneral: k_bwd_base_df<kGeneral><<<grid, kThreads, 0, s>>>(a); break;
-        case kParity4: k_bwd_base_df<kParity4><<<grid, kThreads, 0, s>>>(a); break;
+        case kGeneral: k_bwd_base_df2<kGeneral><<<grid, kThreads, 0, s>>>(a); break;
+        case kParity4: k_bwd_base_df2<kParity4><<<grid, kThreads, 0, s>>>(a); break;
         default: k_bwd_base_df<kParity2><<<grid, kThreads, 0, s>>>(a); break;
     }
 }
