@@ -186,6 +186,16 @@ rq_status rq_hessian(rq_ctx *ctx, const double *gates, double *f, double *egrad,
  * invariant. */
 rq_status rq_set_translation(rq_ctx *ctx, int shift_sites);
 
+/* Checkpointing of the forward pass (memory vs recomputation).  interval 1
+ * (default): every intermediate state of a tile is kept (the paper's
+ * forward-pass cache, Fig. forward_pass).  interval r > 1: only the state at
+ * the start of every segment of r gates is kept, plus one segment buffer; the
+ * backward pass recomputes each segment from its checkpoint (about g / r + r
+ * instead of g + 1 states per tile, for one extra forward sweep).  Results are
+ * bitwise those of interval 1.  The workspace is reallocated (the tile size may
+ * grow); rq_hessian needs interval 1.  0 is read as 1. */
+rq_status rq_set_checkpointing(rq_ctx *ctx, int interval);
+
 /* Arithmetic of the sweep kernels (forward, adjoint, environments).
  * RQ_ARITH_FP64 (default): IEEE binary64 on the FP64 pipe.  RQ_ARITH_DF64:
  * every amplitude and gate entry is kept as an unevaluated sum of two floats

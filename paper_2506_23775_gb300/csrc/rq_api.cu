@@ -73,6 +73,8 @@ struct rq_ctx {
     int space = 0;  // 0 Riemannian outputs, 1 Euclidean (rq_set_gradient_space)
     int arith = 0;  // 0 FP64 sweeps, 1 double-float sweeps (rq_set_arithmetic)
     // translation-representative basis sums (rq_set_translation)
+    int ckpt_r = 1;  // store psi at every ckpt_r-th gate; recompute the rest in the backward pass
+    long long alloc_slots = 0;
     int tshift = 0;
     std::vector<int32_t> reps;     // orbit representatives, ascending
     std::vector<double> rep_w;     // orbit sizes
@@ -254,8 +256,17 @@ void column_groups(const rq_ctx *ctx, std::vector<std::vector<int32_t>> &groups,
     }
 }
 
+// State slots of one checkpoint set: every gate (interval 1), or one
+// checkpoint per segment of `interval` gates plus a segment buffer.
+long long state_slots(const rq_ctx *ctx) {
+    const int r = ctx->ckpt_r;
+    if (r <= 1) return ctx->g + 1;
+    const long long nseg = (ctx->g + r - 1) / r;
+    return nseg + r + 1;
+}
+
 long long bytes_per_column(const rq_ctx *ctx, int kc) {
-    const long long sets = (long long)(1 + kc) * (ctx->g + 1) + 1 + kc;
+    const long long sets = (long long)(1 + kc) * state_slots(ctx) + 1 + kc;
     return sets * ctx->n_store * (long long)sizeof(double2);
 }
 
@@ -307,16 +318,18 @@ rq_status rebuild_tiles(rq_ctx *ctx) {
             tpar.push_back(gpar[gi]);
         }
     }
-    const bool same = ctx->d_psi && B == ctx->B && kc == ctx->kc && ncta == ctx->ncta;
+    const bool same = ctx->d_psi && B == ctx->B && kc == ctx->kc && ncta == ctx->ncta &&
+                      ctx->alloc_slots == state_slots(ctx);
     if (!same) {
         free_workspace(ctx);
         ctx->B = B;
         ctx->log2B = ilog2(B);
         ctx->kc = kc;
         ctx->ncta = ncta;
+        ctx->alloc_slots = state_slots(ctx);
         const long long tile = ctx->n_store * B;
-        RQ_TRY(dev_alloc(ctx, &ctx->d_psi, tile * (ctx->g + 1), ctx->work_bytes));
-        RQ_TRY(dev_alloc(ctx, &ctx->d_dpsi, tile * (ctx->g + 1) * kc, ctx->work_bytes));
+        RQ_TRY(dev_alloc(ctx, &ctx->d_psi, tile * state_slots(ctx), ctx->work_bytes));
+        RQ_TRY(dev_alloc(ctx, &ctx->d_dpsi, tile * state_slots(ctx) * kc, ctx->work_bytes));
         RQ_TRY(dev_alloc(ctx, &ctx->d_lam, tile, ctx->work_bytes));
         RQ_TRY(dev_alloc(ctx, &ctx->d_dlam, tile * kc, ctx->work_bytes));
         RQ_TRY(dev_alloc(ctx, &ctx->d_part, (long long)ctx->g * ncta * rq::kEnvDoubles, ctx->work_bytes));
@@ -569,7 +582,14 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
     const double2 *dsrc = df ? ctx->d_dirs_df : ctx->d_dirs;
     const int B = ctx->B;
     const long long tile = ctx->n_store * B;
-    const long long set = tile * (g + 1);  // one checkpoint set
+    // State slots: interval 1 keeps psi_l in slot l (the paper's forward-pass
+    // cache).  Interval r > 1 keeps psi at the start of every segment of r
+    // gates (slots 0 .. nseg-1) plus a segment buffer (slots nseg .. nseg+r);
+    // the backward pass recomputes each segment from its checkpoint with the
+    // same kernels, so the results are bitwise those of interval 1.
+    const int r = ctx->ckpt_r;
+    const int nseg = (g + r - 1) / r;
+    const long long set = tile * state_slots(ctx);  // one checkpoint set
     const bool backward = want_env || k > 0;
     const int n_chunks = k == 0 ? 1 : (k + ctx->kc - 1) / ctx->kc;
     for (int ch = 0; ch < n_chunks; ++ch) {
@@ -580,22 +600,14 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
             const int32_t *cols = ctx->d_cols + (long long)ti * B;
             const double *wts = ctx->tshift > 0 ? ctx->d_wts + (long long)ti * B : nullptr;
             const int par = ctx->tile_parity[ti];
-            RQ_CUDA(cudaMemsetAsync(ctx->d_psi, 0, sizeof(double2) * tile, s));
-            {
-                ProfScope ps(ctx, kFamInit, 0.0, (double)B * sizeof(double2));
-                if (df) rq::launch_init_unit_df64(ctx->d_psi, cols, B, ctx->log2B, ctx->n_store, s);
-                else rq::launch_init_unit(ctx->d_psi, cols, B, ctx->log2B, ctx->n_store, ctx->structure, s);
-            }
-            RQ_LAUNCHED();
-            for (int d = 0; d < kd; ++d) RQ_CUDA(cudaMemsetAsync(ctx->d_dpsi + d * set, 0, sizeof(double2) * tile, s));
-            // forward pass
-            for (int l = 0; l < g; ++l) {
+            // gate l from slot si to slot so (with the tangents of this chunk)
+            auto fwd = [&](int l, long long si, long long so) -> rq_status {
                 const GateGeom &geo = ctx->geo[l];
                 rq::FwdArgs a;
-                a.psi_in = ctx->d_psi + l * tile;
-                a.psi_out = ctx->d_psi + (l + 1) * tile;
-                a.dpsi_in = ctx->d_dpsi + l * tile;
-                a.dpsi_out = ctx->d_dpsi + (l + 1) * tile;
+                a.psi_in = ctx->d_psi + si * tile;
+                a.psi_out = ctx->d_psi + so * tile;
+                a.dpsi_in = ctx->d_dpsi + si * tile;
+                a.dpsi_out = ctx->d_dpsi + so * tile;
                 a.dir_stride = set;
                 a.kdirs = kd;
                 a.gate = gsrc + (long long)geo.param * 16;
@@ -614,6 +626,40 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                     else rq::launch_fwd(a, ctx->ncta, s);
                 }
                 RQ_LAUNCHED();
+                return RQ_OK;
+            };
+            auto copy_slot = [&](long long from, long long to) -> rq_status {
+                RQ_CUDA(cudaMemcpyAsync(ctx->d_psi + to * tile, ctx->d_psi + from * tile, sizeof(double2) * tile,
+                                        cudaMemcpyDeviceToDevice, s));
+                for (int d = 0; d < kd; ++d)
+                    RQ_CUDA(cudaMemcpyAsync(ctx->d_dpsi + d * set + to * tile, ctx->d_dpsi + d * set + from * tile,
+                                            sizeof(double2) * tile, cudaMemcpyDeviceToDevice, s));
+                return RQ_OK;
+            };
+            const long long slot0 = r == 1 ? 0 : nseg;
+            RQ_CUDA(cudaMemsetAsync(ctx->d_psi + slot0 * tile, 0, sizeof(double2) * tile, s));
+            {
+                ProfScope ps(ctx, kFamInit, 0.0, (double)B * sizeof(double2));
+                if (df) rq::launch_init_unit_df64(ctx->d_psi + slot0 * tile, cols, B, ctx->log2B, ctx->n_store, s);
+                else rq::launch_init_unit(ctx->d_psi + slot0 * tile, cols, B, ctx->log2B, ctx->n_store, ctx->structure, s);
+            }
+            RQ_LAUNCHED();
+            for (int d = 0; d < kd; ++d)
+                RQ_CUDA(cudaMemsetAsync(ctx->d_dpsi + d * set + slot0 * tile, 0, sizeof(double2) * tile, s));
+            // forward pass
+            long long final_slot = g;
+            if (r == 1) {
+                for (int l = 0; l < g; ++l) RQ_TRY(fwd(l, l, l + 1));
+            } else {
+                int prev_len = 0;
+                for (int sg = 0; sg < nseg; ++sg) {
+                    const int base = sg * r, len = std::min(r, g - base);
+                    if (sg > 0) RQ_TRY(copy_slot(nseg + prev_len, nseg));
+                    RQ_TRY(copy_slot(nseg, sg));  // checkpoint of the segment start
+                    for (int i = 0; i < len; ++i) RQ_TRY(fwd(base + i, nseg + i, nseg + i + 1));
+                    prev_len = len;
+                }
+                final_slot = nseg + prev_len;
             }
             // adjoint start lambda_g = U|j> and the cost summands
             RQ_CUDA(cudaMemsetAsync(ctx->d_lam, 0, sizeof(double2) * tile, s));
@@ -621,10 +667,10 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                 ProfScope ps(ctx, kFamTarget, 0.0, 0.0);
                 if (df)
                     rq::launch_scatter_target_df64(target_dev(ctx), cols, wts, B, ctx->log2B, ctx->structure, ctx->n,
-                                                   ctx->d_lam, ctx->d_psi + g * tile, ctx->d_fpart, s);
+                                                   ctx->d_lam, ctx->d_psi + final_slot * tile, ctx->d_fpart, s);
                 else
                     rq::launch_scatter_target(target_dev(ctx), cols, wts, B, ctx->log2B, ctx->structure, ctx->n,
-                                              ctx->d_lam, ctx->d_psi + g * tile, ctx->d_fpart, s);
+                                              ctx->d_lam, ctx->d_psi + final_slot * tile, ctx->d_fpart, s);
             }
             RQ_LAUNCHED();
             if (first) {
@@ -637,11 +683,12 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
             if (!backward) continue;
             for (int d = 0; d < kd; ++d) RQ_CUDA(cudaMemsetAsync(ctx->d_dlam + d * tile, 0, sizeof(double2) * tile, s));
             const bool acc_env = want_env && first;
-            for (int l = g - 1; l >= 0; --l) {
+            // backward step of gate l with psi_l (and its tangents) in slot sl
+            auto bwd = [&](int l, long long sl) -> rq_status {
                 const GateGeom &geo = ctx->geo[l];
                 rq::BwdArgs a;
                 a.lam = ctx->d_lam;
-                a.psi = ctx->d_psi + l * tile;
+                a.psi = ctx->d_psi + sl * tile;
                 a.gate = gsrc + (long long)geo.param * 16;
                 a.geo = geo;
                 a.log2B = ctx->log2B;
@@ -651,7 +698,7 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                 for (int d = 0; d < kd; ++d) {
                     rq::BwdArgs b = a;
                     b.dlam = ctx->d_dlam + d * tile;
-                    b.dpsi = ctx->d_dpsi + d * set + l * tile;
+                    b.dpsi = ctx->d_dpsi + d * set + sl * tile;
                     b.dir = dsrc + ((long long)(d0 + d) * P + geo.param) * 16;
                     b.accumulate = 1;
                     b.part = ctx->d_partd + ((long long)d * g + l) * ctx->ncta * rq::kEnvDoubles;
@@ -680,6 +727,19 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                         else rq::launch_bwd_base(a, ctx->ncta, s);
                     }
                     RQ_LAUNCHED();
+                }
+                return RQ_OK;
+            };
+            if (r == 1) {
+                for (int l = g - 1; l >= 0; --l) RQ_TRY(bwd(l, l));
+            } else {
+                for (int sg = nseg - 1; sg >= 0; --sg) {
+                    const int base = sg * r, len = std::min(r, g - base);
+                    if (sg < nseg - 1) {  // recompute the segment from its checkpoint
+                        RQ_TRY(copy_slot(sg, nseg));
+                        for (int i = 0; i < len; ++i) RQ_TRY(fwd(base + i, nseg + i, nseg + i + 1));
+                    }
+                    for (int l = base + len - 1; l >= base; --l) RQ_TRY(bwd(l, nseg + (l - base)));
                 }
             }
             if (acc_env) {
@@ -890,6 +950,7 @@ rq_status rq_setup_target(rq_ctx *ctx, const rq_target *tgt, const rq_circuit *c
     ctx->c0 = 0;
     ctx->c1 = 1LL << ctx->n;
     ctx->tshift = 0;
+    ctx->ckpt_r = 1;
     ctx->reps.clear();
     ctx->rep_w.clear();
     ctx->ready = true;
@@ -927,6 +988,8 @@ rq_status rq_hessian(rq_ctx *ctx, const double *gates, double *f, double *egrad,
     if (!ctx) return RQ_EINVAL;
     if (!ctx->ready) return fail(ctx, RQ_ESTATE, "no target set up");
     if (!gates || !hess) return fail(ctx, RQ_EINVAL, "gates or hess is NULL");
+    if (ctx->ckpt_r != 1)
+        return fail(ctx, RQ_EINVAL, "the full Hessian keeps every state: set the checkpoint interval to 1");
     RQ_TRY(ensure_small(ctx, 1));
     cudaStream_t s = ctx->stream;
     const int g = ctx->g, P = ctx->P, B = ctx->B;
@@ -1154,6 +1217,14 @@ rq_status rq_set_translation(rq_ctx *ctx, int shift_sites) {
         ctx->rep_w.push_back((double)size);
     }
     ctx->tshift = shift_sites;
+    return rebuild_tiles(ctx);
+}
+
+rq_status rq_set_checkpointing(rq_ctx *ctx, int interval) {
+    if (!ctx) return RQ_EINVAL;
+    if (!ctx->ready) return fail(ctx, RQ_ESTATE, "no target set up");
+    if (interval < 0) return fail(ctx, RQ_EINVAL, "checkpoint interval %d < 0", interval);
+    ctx->ckpt_r = std::max(1, std::min(interval, ctx->g));
     return rebuild_tiles(ctx);
 }
 

@@ -24,7 +24,8 @@ EXPORTS = ("rq_create", "rq_destroy", "rq_setup_target", "rq_set_columns", "rq_s
            "rq_tr_step", "rq_target_column", "rq_get_info", "rq_profile_start", "rq_profile_stop",
            "rq_cost_static", "rq_set_gradient_space", "rq_batch_create", "rq_batch_destroy",
            "rq_batch_add", "rq_batch_set_tile", "rq_batch_hvp", "rq_batch_info", "rq_batch_last_error",
-           "rq_set_arithmetic", "rq_set_translation", "rq_hessian", "rq_last_error")
+           "rq_set_arithmetic", "rq_set_translation", "rq_hessian", "rq_set_checkpointing",
+           "rq_last_error")
 
 
 class RQCircuit(C.Structure):
@@ -96,6 +97,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "rq_set_arithmetic": ([vp, C.c_int], C.c_int),
         "rq_set_translation": ([vp, C.c_int], C.c_int),
         "rq_hessian": ([vp, dp, dp, dp, dp], C.c_int),
+        "rq_set_checkpointing": ([vp, C.c_int], C.c_int),
         "rq_batch_create": ([C.POINTER(vp), C.c_int], C.c_int),
         "rq_batch_destroy": ([vp], C.c_int),
         "rq_batch_add": ([vp, C.POINTER(RQTarget), C.POINTER(RQCircuit), C.POINTER(C.c_int)], C.c_int),
@@ -195,6 +197,11 @@ class Context:
     def set_arithmetic(self, arith: int):
         """0: FP64 sweeps (default); 1: double-float sweeps on the FP32 pipe."""
         self._check(self._lib.rq_set_arithmetic(self._h, int(arith)))
+
+    def set_checkpointing(self, interval: int):
+        """Keep the forward state every ``interval`` gates (1: every gate) and
+        recompute the rest in the backward pass."""
+        self._check(self._lib.rq_set_checkpointing(self._h, int(interval)))
 
     def set_translation(self, shift_sites: int):
         """Sum over translation-orbit representatives (0: plain basis sums)."""
