@@ -192,8 +192,10 @@ rq_status rq_set_translation(rq_ctx *ctx, int shift_sites);
  * the start of every segment of r gates is kept, plus one segment buffer; the
  * backward pass recomputes each segment from its checkpoint (about g / r + r
  * instead of g + 1 states per tile, for one extra forward sweep).  Results are
- * bitwise those of interval 1.  The workspace is reallocated (the tile size may
- * grow); rq_hessian needs interval 1.  0 is read as 1. */
+ * bitwise those of interval 1.  interval 0 (default): automatic -- every
+ * state unless that would force tiles below min(256, columns), then a
+ * checkpoint every ceil(sqrt(g)) gates.  The workspace is reallocated (the
+ * tile size may grow); rq_hessian needs an effective interval of 1. */
 rq_status rq_set_checkpointing(rq_ctx *ctx, int interval);
 
 /* Arithmetic of the sweep kernels (forward, adjoint, environments).

@@ -73,7 +73,8 @@ struct rq_ctx {
     int space = 0;  // 0 Riemannian outputs, 1 Euclidean (rq_set_gradient_space)
     int arith = 0;  // 0 FP64 sweeps, 1 double-float sweeps (rq_set_arithmetic)
     // translation-representative basis sums (rq_set_translation)
-    int ckpt_r = 1;  // store psi at every ckpt_r-th gate; recompute the rest in the backward pass
+    int ckpt_r = 1;    // effective: store psi at every ckpt_r-th gate, recompute the rest
+    int ckpt_req = 0;  // requested interval (0: automatic, from the memory budget)
     long long alloc_slots = 0;
     int tshift = 0;
     std::vector<int32_t> reps;     // orbit representatives, ascending
@@ -289,15 +290,25 @@ rq_status rebuild_tiles(rq_ctx *ctx) {
     int B = 0, kc = 1;
     const int kc_opts[2] = {rq::kMaxDirs, 1};
     const int n_opts = ctx->user_kc > 0 ? 1 : 2;
-    for (int o = 0; o < n_opts; ++o) {
-        const int k = ctx->user_kc > 0 ? ctx->user_kc : kc_opts[o];
-        int b = bcap;
-        while (b > 1 && (double)b * bytes_per_column(ctx, k) > budget) b >>= 1;
-        if ((double)b * bytes_per_column(ctx, k) > budget) continue;
-        if (o + 1 < n_opts && b < std::min(bcap, 256)) continue;
-        B = b;
-        kc = k;
-        break;
+    // automatic checkpointing: keep every state unless that forces tiles
+    // below min(bcap, 256) columns; then a checkpoint every ~sqrt(g) gates
+    // (about 2 sqrt(g) states per tile instead of g + 1)
+    int r_opts[2] = {1, std::max(2, (int)std::ceil(std::sqrt((double)ctx->g)))};
+    const int n_r = ctx->ckpt_req > 0 ? 1 : 2;
+    if (ctx->ckpt_req > 0) r_opts[0] = std::max(1, std::min(ctx->ckpt_req, ctx->g));
+    for (int ri = 0; ri < n_r && B == 0; ++ri) {
+        ctx->ckpt_r = r_opts[ri];
+        for (int o = 0; o < n_opts; ++o) {
+            const int k = ctx->user_kc > 0 ? ctx->user_kc : kc_opts[o];
+            int b = bcap;
+            while (b > 1 && (double)b * bytes_per_column(ctx, k) > budget) b >>= 1;
+            if ((double)b * bytes_per_column(ctx, k) > budget) continue;
+            if (o + 1 < n_opts && b < std::min(bcap, 256)) continue;
+            if (ri + 1 < n_r && b < std::min(bcap, 256)) continue;
+            B = b;
+            kc = k;
+            break;
+        }
     }
     if (B == 0)
         return fail(ctx, RQ_ENOMEM, "one column needs %lld bytes of workspace, %.0f available",
@@ -951,6 +962,7 @@ rq_status rq_setup_target(rq_ctx *ctx, const rq_target *tgt, const rq_circuit *c
     ctx->c1 = 1LL << ctx->n;
     ctx->tshift = 0;
     ctx->ckpt_r = 1;
+    ctx->ckpt_req = 0;
     ctx->reps.clear();
     ctx->rep_w.clear();
     ctx->ready = true;
@@ -989,7 +1001,8 @@ rq_status rq_hessian(rq_ctx *ctx, const double *gates, double *f, double *egrad,
     if (!ctx->ready) return fail(ctx, RQ_ESTATE, "no target set up");
     if (!gates || !hess) return fail(ctx, RQ_EINVAL, "gates or hess is NULL");
     if (ctx->ckpt_r != 1)
-        return fail(ctx, RQ_EINVAL, "the full Hessian keeps every state: set the checkpoint interval to 1");
+        return fail(ctx, RQ_EINVAL, "the full Hessian keeps every state, but the workspace keeps one every %d "
+                    "gates: set the checkpoint interval to 1 (a smaller tile if memory is short)", ctx->ckpt_r);
     RQ_TRY(ensure_small(ctx, 1));
     cudaStream_t s = ctx->stream;
     const int g = ctx->g, P = ctx->P, B = ctx->B;
@@ -1224,7 +1237,7 @@ rq_status rq_set_checkpointing(rq_ctx *ctx, int interval) {
     if (!ctx) return RQ_EINVAL;
     if (!ctx->ready) return fail(ctx, RQ_ESTATE, "no target set up");
     if (interval < 0) return fail(ctx, RQ_EINVAL, "checkpoint interval %d < 0", interval);
-    ctx->ckpt_r = std::max(1, std::min(interval, ctx->g));
+    ctx->ckpt_req = interval;
     return rebuild_tiles(ctx);
 }
 

@@ -33,9 +33,10 @@ def test_recompute_is_bitwise_equal(rq, name, structure, arith, cols):
         got = ctx.hvp(prob.gates, X)
         assert got[0] == ref[0], r
         assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2]), r
-        if r == 7 and ctx.info()["columns_per_tile"] == 1:
-            pass
     ctx.set_checkpointing(7)
     assert ctx.info()["workspace_bytes"] <= bytes1
     with pytest.raises(rq.RQError):
         ctx.hessian(prob.gates)
+    ctx.set_checkpointing(1)
+    ctx.set_tile(0, 2)
+    assert ctx.hvp(prob.gates, X)[0] == ref[0]
