@@ -94,7 +94,7 @@ struct rq_ctx {
 
 namespace {
 
-std::string g_create_error;
+thread_local std::string g_create_error;  // text of the last rq_create failure of this thread
 
 enum Family : int { kFamFwd = 0, kFamBwdDir, kFamBwdBase, kFamTarget, kFamInit, kFamReduce, kFamGeometry, kFamCheb, kFamCount };
 const char *const kFamilyName[kFamCount] = {"fwd_gate", "bwd_gate_dir", "bwd_gate_base", "target_scatter_cost",
