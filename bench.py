@@ -390,7 +390,12 @@ def run_ours(args):
                     "peak_source": "derived: 128 FP32 lanes x 152 SMs x 2.07 GHz",
                     "fp64_equivalent_tflops": round(achieved, 4), "launch_ms": round(per_launch_ms, 4),
                     "hbm_achieved_gbs": round(d["bytes"] / (d["ms"] * 1e-3) / 1e9, 1),
-                    "hbm_frac": round(d["bytes"] / (d["ms"] * 1e-3) / 1e9 / hbm, 4)}
+                    "hbm_frac": round(d["bytes"] / (d["ms"] * 1e-3) / 1e9 / hbm, 4),
+                    "families": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                                     "share": round(v["ms"] / sum(x["ms"] for x in res["prof"].values()), 4),
+                                     "fp32_pipe_frac": round(v["flops"] * 6.0 / max(v["ms"], 1e-9) / 1e9
+                                                             / FP32_PIPE_TOPS, 4)}
+                                 for k, v in res["prof"].items()}}
         fam = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                    "share": round(v["ms"] / sum(x["ms"] for x in res["prof"].values()), 4),
                    "tflops": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 4),
