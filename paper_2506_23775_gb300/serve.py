@@ -49,6 +49,22 @@ def problem_key(p) -> tuple:
             p.pairs.tobytes(), p.param_of.tobytes())
 
 
+def work_flops(req: "Request") -> float:
+    """FP64 flops of one request: 1 / 3 / 9 gate passes per gate for cost /
+    gradient / HVP, 32 flops per amplitude and column (a quarter for parity
+    gates), over the full basis."""
+    p = req.problem
+    units = {"cost": 1, "grad": 3, "hvp": 9}[req.kind]
+    return units * p.n_gates * 32.0 * 4.0 ** p.n / (4.0 if p.structure == 1 else 1.0)
+
+
+def gpu_width(p, tile: int, sms: int = 152) -> float:
+    """Fraction of the GPU one sweep kernel of this problem fills (its items
+    over two 256-thread CTAs per SM)."""
+    n_store = (1 << (p.n - 1)) if p.structure == 1 else (1 << p.n)
+    return min(1.0, n_store / 4 * tile / (sms * 2 * 256))
+
+
 def footprint_bytes(p, tile: int, k: int = 1) -> int:
     """Device bytes of a problem's context: target blocks, tables, workspace."""
     n_store = (1 << (p.n - 1)) if p.structure == 1 else (1 << p.n)
@@ -77,7 +93,8 @@ class Server:
     """
 
     def __init__(self, device: int = 0, memory_budget: Optional[int] = None, max_inflight: int = 8,
-                 tile: int = 128, contexts_per_problem: int = 2, setup_workers: int = 2):
+                 tile: int = 128, contexts_per_problem: int = 2, setup_workers: int = 2,
+                 policy: str = "sjf"):
         import concurrent.futures as cf
 
         import torch
@@ -97,6 +114,8 @@ class Server:
         self.held = 0
         self.stats = collections.Counter()
         self.pool = cf.ThreadPoolExecutor(max_workers=setup_workers)
+        self.policy = policy
+        self.sms = torch.cuda.get_device_properties(self.dev).multi_processor_count
 
     # -- contexts ----------------------------------------------------------
     def _evict_idle(self, need: int) -> bool:
@@ -186,11 +205,17 @@ class Server:
             while pending and (not realtime or pending[0].arrival <= t):
                 waiting.append(pending.popleft())
             self._harvest_builds()
-            # admit as slots and memory allow (first come, first served; a
-            # request whose problem has no free context does not block others)
+            # admit as slots and memory allow.  "fifo": arrival order.  "sjf":
+            # shortest work first, and a new request joins only while the
+            # in-flight sweeps do not already fill the GPU (a saturated FP64
+            # pipe gains nothing from overlap, and sharing it delays everyone).
+            # A request whose problem has no free context does not block others.
+            if self.policy == "sjf":
+                waiting.sort(key=work_flops)
+            width = sum(gpu_width(r.problem, s.tile, self.sms) for r, s, _, _ in inflight)
             still = []
             for req in waiting:
-                if len(inflight) >= self.max_inflight:
+                if len(inflight) >= self.max_inflight or (self.policy == "sjf" and inflight and width >= 1.0):
                     still.append(req)
                     continue
                 s = self._slot_for(req)
@@ -201,6 +226,7 @@ class Server:
                 req.admitted = now()
                 ev, out = self._launch(req, s)
                 inflight.append((req, s, ev, out))
+                width += gpu_width(req.problem, s.tile, self.sms)
             waiting = still
             # collect finished work
             rest = []
