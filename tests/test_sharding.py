@@ -74,3 +74,43 @@ def test_two_rank_gloo_sum_matches_unsharded(tmp_path):
     assert abs(float(r["f"]) - f) <= 1e-13 * abs(f)
     np.testing.assert_allclose(r["g"], g, atol=1e-13 * np.abs(g).max())
     np.testing.assert_allclose(r["hv"], hv, atol=1e-13 * np.abs(hv).max())
+
+
+def _failing_worker(rank, world, port, out_path):
+    import datetime
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=20))
+    if rank == 1:
+        # this rank fails on the host before the exchange (no device work in flight)
+        os._exit(3)
+    try:
+        shard.sharded_eval(lambda c0, c1: (1.0, np.zeros((1, 4, 4), np.complex128), None), 16, 1, 0)
+        status = "completed"
+    except Exception as e:  # the surviving rank learns of the failure from the collective
+        status = "error: " + type(e).__name__
+    with open(out_path, "w") as fh:
+        fh.write(status)
+    os._exit(0)
+
+
+def test_a_failed_rank_is_reported_not_hung(tmp_path):
+    import subprocess
+    import sys
+    import time
+    out = str(tmp_path / "status.txt")
+    port = _free_port()
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from tests.test_sharding import _failing_worker\n"
+        "import torch.multiprocessing as mp\n"
+        "mp.start_processes(_failing_worker, args=(2, %d, %r), nprocs=2, join=False, start_method='spawn')\n"
+        "import time; time.sleep(0.1)\n" % (os.path.dirname(os.path.dirname(os.path.abspath(__file__))), port, out))
+    t0 = time.time()
+    proc = subprocess.Popen([sys.executable, "-c", code])
+    deadline = t0 + 120
+    while time.time() < deadline and not os.path.exists(out):
+        time.sleep(0.2)
+    proc.wait(timeout=30)
+    assert os.path.exists(out), "the surviving rank neither finished nor reported the failure"
+    assert open(out).read().startswith("error"), open(out).read()
