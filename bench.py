@@ -37,6 +37,24 @@ FP64_PEAK_TFLOPS = 4 * 152 * 2.07e9 / 1e12
 FP32_PIPE_TOPS = 128 * 152 * 2.07e9 / 1e12   # FP32 pipe instructions per second (one FMA = one)
 HBM_FALLBACK_GBS = 6800.0
 
+# DRAM traffic of one FP64 bwd_gate_dir launch of this workload (2^14 x 512
+# items: n = 16, general gates, 512-column tile), dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of the full-size launch
+# (profiles/bwd_gate_dir_n16_tile512_dram.md).  It holds only for the kernel
+# source it was taken on, so the sources are hashed and compared at run time.
+TRAFFIC = {"kernel": "bwd_gate_dir", "bytes_per_launch": None, "sha256": None,
+           "sources": ("paper_2506_23775_gb300/csrc/rq_sweep.cu", "paper_2506_23775_gb300/csrc/rq_internal.h")}
+
+
+def _kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 WORKLOAD = ("spinful Fermi-Hubbard chain, 8 sites (n=16 qubits), open, J=1 U=4 t=0.5; "
             "brickwall 11 layers ABCBABCBABC, 78 U(4) gates (Trotter + noise, seed 1601); "
             "f + Riemannian grad + 1 Riemannian HVP (direction seed 1602) summed over all 65536 basis columns")
@@ -383,10 +401,14 @@ def run_ours(args):
 
     hbm, hbm_src = _measured_hbm()
 
-    def roofline(res, df64=False):
+    def roofline(res, df64=False, headline=False):
         sweep = {k: v for k, v in res["prof"].items() if k.startswith(("fwd", "bwd"))}
         dom = max(sweep, key=lambda k: sweep[k]["ms"])
         d = sweep[dom]
+        traffic = None
+        if (headline and TRAFFIC["bytes_per_launch"] and dom == TRAFFIC["kernel"] and res["B"] == 512
+                and (args.sites, args.depth) == (8, 11) and _kernel_sources_sha256() == TRAFFIC["sha256"]):
+            traffic = TRAFFIC["bytes_per_launch"]
         per_launch_ms = d["ms"] / d["launches"]
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
         if df64:
@@ -409,7 +431,8 @@ def run_ours(args):
                    "tflops": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 4),
                    "gbs": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)} for k, v in res["prof"].items()}
         return {"kernel": dom, "bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
                 "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (FP64)",
                 "flops_per_launch": d["flops"] / d["launches"], "launch_ms": round(per_launch_ms, 4),
                 "hbm_achieved_gbs": round(d["bytes"] / (d["ms"] * 1e-3) / 1e9, 1),
@@ -424,7 +447,7 @@ def run_ours(args):
                    "columns_per_tile": gen["B"], "hvp_directions": 1,
                    "l2": "inputs larger than L2 (each tile state is 512 MiB)",
                    "parallelism": f"column shards x{world}" if world > 1 else "single GPU"},
-        "roofline": roofline(gen), "e2e": gen["e2e"], "gpu_launches": gen["launches"], "clocks": gen["clocks"],
+        "roofline": roofline(gen, headline=True), "e2e": gen["e2e"], "gpu_launches": gen["launches"], "clocks": gen["clocks"],
     }
     if par is not None:
         line["parity"] = {"value": par["value"], "unit": UNIT, "ms_per_step": par["ms_per_step"],

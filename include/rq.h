@@ -76,7 +76,16 @@ typedef struct {
  * wrap bond without Z string when periodic, Eq. slFH_qubit), on-site U;
  * n_qubits = 2 * n_sites.  model 1: spinless chain in its hard-core boson
  * form (Eq. slFH_qubit): hopping -J and nearest-neighbour interaction
- * U n_j n_{j+1} on every bond (wrap bond if periodic); n_qubits = n_sites. */
+ * U n_j n_{j+1} on every bond (wrap bond if periodic); n_qubits = n_sites.
+ * model 2: any dense target matrix (the cost of Eq. f_target_sum_unit_vec
+ * with U given entry by entry, for tests and for targets that are not a
+ * chain Hamiltonian's evolution): dense_U points to 2^n x 2^n complex128
+ * values, row-major, interleaved (re, im), 2 <= n_qubits <= 14; n_sites,
+ * periodic, J, U and t are ignored.  The matrix is copied during
+ * rq_setup_target and not referenced afterwards.  With parity gates only its
+ * two parity-diagonal blocks are used (the circuit keeps each column in its
+ * parity sector, so the other entries do not enter f).  Models 0 and 1 leave
+ * dense_U unread (NULL is fine). */
 typedef struct {
     int model;
     int n_sites;
@@ -84,6 +93,7 @@ typedef struct {
     double J;
     double U;
     double t;
+    const double *dense_U;
 } rq_target;
 
 /* One trust-region iteration (Absil et al. Algorithm 10 with truncated CG,
@@ -185,6 +195,26 @@ rq_status rq_hessian(rq_ctx *ctx, const double *gates, double *f, double *egrad,
  * is open, the shift does not divide the sites, or the circuit is not
  * invariant. */
 rq_status rq_set_translation(rq_ctx *ctx, int shift_sites);
+
+/* Gate validation, off by default.  With enable = 1 every rq_cost, rq_grad,
+ * rq_hvp, rq_tr_step (each evaluation inside it) and rq_hessian call, and
+ * the _dev variants (which then copy the gates to the host and synchronise
+ * the stream), first checks each parameter gate: finite entries,
+ * ||G^H G - I||_F <= 1e-10 (the gates are points of U(4), Sec. "Riemannian
+ * optimization"), and for parity gates (Eq. paritygatematrix) no entry above
+ * 1e-10 outside the parity pattern.  A failed check returns RQ_EINVAL with the
+ * gate index and the deviation in rq_last_error, before any launch.  The
+ * batch and rq_cost_static calls do not check. */
+rq_status rq_set_checks(rq_ctx *ctx, int enable);
+
+/* CUDA graphs for the host-memory calls (rq_cost, rq_grad, rq_hvp and the
+ * evaluations inside rq_tr_step): with enable = 1 (default) the kernel
+ * sequence of an evaluation is captured once per (k, kind) and replayed as one
+ * graph launch until the context's configuration changes (columns, tile,
+ * arithmetic, output space, translation, checkpointing, profiling), which
+ * removes the per-kernel launch cost of small problems.  Results are bitwise
+ * those of direct launches.  enable = 0 launches kernels directly. */
+rq_status rq_set_graphs(rq_ctx *ctx, int enable);
 
 /* Checkpointing of the forward pass (memory vs recomputation).  interval 1
  * (default): every intermediate state of a tile is kept (the paper's

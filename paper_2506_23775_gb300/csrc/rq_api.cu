@@ -90,6 +90,17 @@ struct rq_ctx {
     bool prof_on = false;
     std::vector<ProfRec> prof;
     size_t prof_used = 0;
+    // CUDA graphs of host-memory evaluations, keyed by (k, env_mode); an entry
+    // is valid while the context's configuration version is unchanged
+    struct GraphEntry {
+        cudaGraphExec_t exec = nullptr;
+        int k = -1, env = -1;
+        long long version = -1, launches = 0, last_use = 0;
+    };
+    std::vector<GraphEntry> graphs;
+    bool use_graphs = true;
+    long long version = 0, graph_clock = 0;
+    int checks = 0;  // validate the gates of every call (unitarity, parity pattern)
 };
 
 namespace {
@@ -203,8 +214,16 @@ void free_small(rq_ctx *ctx) {
     ctx->small_bytes = 0;
 }
 
+void drop_graphs(rq_ctx *ctx) {
+    for (auto &e : ctx->graphs)
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+    ctx->graphs.clear();
+}
+
 void free_problem(rq_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    drop_graphs(ctx);
+    ++ctx->version;
     free_workspace(ctx);
     free_small(ctx);
     dev_free(ctx->d_sec_of);
@@ -274,7 +293,32 @@ long long bytes_per_column(const rq_ctx *ctx, int kc) {
 // Choose B (columns per tile) and kc (directions per sweep), build the tile
 // column table and (re)allocate the sweep workspace.  A new column range with
 // the same B and kc only re-uploads the column table.
+// Everything a captured evaluation depends on besides the contents of the
+// column table: buffer addresses, tile geometry, the segment structure.
+std::vector<long long> tile_layout(const rq_ctx *ctx) {
+    std::vector<long long> v = {(long long)(uintptr_t)ctx->d_psi, (long long)(uintptr_t)ctx->d_dpsi,
+                                (long long)(uintptr_t)ctx->d_lam, (long long)(uintptr_t)ctx->d_dlam,
+                                (long long)(uintptr_t)ctx->d_part, (long long)(uintptr_t)ctx->d_partd,
+                                (long long)(uintptr_t)ctx->d_fpart, (long long)(uintptr_t)ctx->d_cols,
+                                (long long)(uintptr_t)ctx->d_wts, ctx->B, ctx->kc, ctx->ncta, ctx->ckpt_r,
+                                ctx->tshift > 0, ctx->n_tiles};
+    v.insert(v.end(), ctx->tile_parity.begin(), ctx->tile_parity.end());
+    return v;
+}
+
+rq_status rebuild_tiles_impl(rq_ctx *ctx);
+
+// New column tables that keep the layout (e.g. the next batch of columns of
+// the same size) keep the captured evaluations: the column indices and
+// weights are read from device memory at run time.
 rq_status rebuild_tiles(rq_ctx *ctx) {
+    const std::vector<long long> before = tile_layout(ctx);
+    const rq_status st = rebuild_tiles_impl(ctx);
+    if (st != RQ_OK || tile_layout(ctx) != before) ++ctx->version;
+    return st;
+}
+
+rq_status rebuild_tiles_impl(rq_ctx *ctx) {
     RQ_CUDA(cudaStreamSynchronize(ctx->stream));
     std::vector<std::vector<int32_t>> groups;
     std::vector<std::vector<double>> gw;
@@ -370,6 +414,7 @@ rq_status rebuild_tiles(rq_ctx *ctx) {
 
 rq_status ensure_small(rq_ctx *ctx, int k) {
     if (k > ctx->dirs_cap) {
+        ++ctx->version;
         RQ_CUDA(cudaStreamSynchronize(ctx->stream));
         dev_free(ctx->d_dirs);
         dev_free(ctx->d_dirs_raw);
@@ -387,6 +432,7 @@ rq_status ensure_small(rq_ctx *ctx, int k) {
     // f at [0], then 16-byte aligned complex outputs from [2]
     const long long need = 2 + (long long)(1 + ctx->dirs_cap) * ctx->P * 32;
     if (need > ctx->out_cap) {
+        ++ctx->version;
         dev_free(ctx->d_out);
         RQ_TRY(dev_alloc(ctx, &ctx->d_out, need, ctx->small_bytes));
         ctx->out_cap = need;
@@ -403,6 +449,60 @@ rq::TargetDev target_dev(const rq_ctx *ctx) {
     t.off_u = ctx->d_off_u;
     t.U = ctx->d_U;
     return t;
+}
+
+// Dense target (model 2): the caller's 2^n x 2^n matrix, row-major.  With
+// general gates it is one block over all basis states.  With parity gates the
+// circuit keeps every column in the parity sector of its basis state, so only
+// the two parity-diagonal blocks of U enter f and its derivatives (the
+// off-diagonal blocks pair with amplitudes that are zero); they are stored as
+// two sectors.  Blocks are stored column by column, like the chain targets.
+rq_status build_target_dense(rq_ctx *ctx, const double *dense) {
+    const int n = ctx->n;
+    const long long dim = 1LL << n;
+    const bool by_parity = ctx->structure == 1;
+    ctx->S = by_parity ? 2 : 1;
+    std::vector<long long> count(ctx->S, 0);
+    ctx->sec_of_h.assign(dim, 0);
+    ctx->pos_h.assign(dim, 0);
+    for (long long x = 0; x < dim; ++x) {
+        const int s = by_parity ? (__builtin_popcountll(x) & 1) : 0;
+        ctx->sec_of_h[x] = s;
+        ctx->pos_h[x] = (int32_t)count[s]++;
+    }
+    ctx->off_basis.assign(ctx->S + 1, 0);
+    ctx->off_u.assign(ctx->S + 1, 0);
+    for (int s = 0; s < ctx->S; ++s) {
+        ctx->off_basis[s + 1] = ctx->off_basis[s] + count[s];
+        ctx->off_u[s + 1] = ctx->off_u[s] + count[s] * count[s];
+    }
+    ctx->basis_h.assign(dim, 0);
+    for (long long x = 0; x < dim; ++x) ctx->basis_h[ctx->off_basis[ctx->sec_of_h[x]] + ctx->pos_h[x]] = (int32_t)x;
+    ctx->u_entries = ctx->off_u[ctx->S];
+    std::vector<double2> blocks((size_t)ctx->u_entries);
+    for (long long j = 0; j < dim; ++j) {
+        const int s = ctx->sec_of_h[j];
+        const long long m = count[s];
+        double2 *col = blocks.data() + ctx->off_u[s] + (long long)ctx->pos_h[j] * m;
+        for (long long r = 0; r < m; ++r) {
+            const long long x = ctx->basis_h[ctx->off_basis[s] + r];
+            col[r] = make_double2(dense[2 * (x * dim + j)], dense[2 * (x * dim + j) + 1]);
+        }
+    }
+    RQ_TRY(dev_alloc(ctx, &ctx->d_sec_of, dim, ctx->problem_bytes));
+    RQ_TRY(dev_alloc(ctx, &ctx->d_pos, dim, ctx->problem_bytes));
+    RQ_TRY(dev_alloc(ctx, &ctx->d_basis, dim, ctx->problem_bytes));
+    RQ_TRY(dev_alloc(ctx, &ctx->d_off_basis, ctx->S + 1, ctx->problem_bytes));
+    RQ_TRY(dev_alloc(ctx, &ctx->d_off_u, ctx->S + 1, ctx->problem_bytes));
+    RQ_TRY(dev_alloc(ctx, &ctx->d_U, ctx->u_entries, ctx->problem_bytes));
+    RQ_CUDA(cudaMemcpyAsync(ctx->d_sec_of, ctx->sec_of_h.data(), dim * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    RQ_CUDA(cudaMemcpyAsync(ctx->d_pos, ctx->pos_h.data(), dim * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    RQ_CUDA(cudaMemcpyAsync(ctx->d_basis, ctx->basis_h.data(), dim * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    RQ_CUDA(cudaMemcpyAsync(ctx->d_off_basis, ctx->off_basis.data(), (ctx->S + 1) * sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
+    RQ_CUDA(cudaMemcpyAsync(ctx->d_off_u, ctx->off_u.data(), (ctx->S + 1) * sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
+    RQ_CUDA(cudaMemcpyAsync(ctx->d_U, blocks.data(), ctx->u_entries * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+    RQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    return RQ_OK;
 }
 
 // Build the per-sector target blocks on the device (Chebyshev expansion).
@@ -785,6 +885,47 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
 
 namespace rq {
 
+// Gate validation (rq_set_checks): every parameter gate finite and unitary,
+// ||G^H G - I||_F <= 1e-10, and for parity gates no entry above 1e-10 outside
+// the parity pattern (the library masks to the pattern; a large entry there
+// means the caller's gates are not the parity gates it declared).
+rq_status check_gates(rq_ctx *ctx, const double *gates) {
+    if (!ctx->checks) return RQ_OK;
+    for (int p = 0; p < ctx->P; ++p) {
+        const double *G = gates + (long long)p * 32;
+        for (int i = 0; i < 32; ++i)
+            if (!std::isfinite(G[i])) return fail(ctx, RQ_EINVAL, "gate %d has a non-finite entry", p);
+        double dev2 = 0.0, off = 0.0;
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) {
+                double re = a == b ? -1.0 : 0.0, im = 0.0;  // (G^H G)[a][b] - I[a][b]
+                for (int r = 0; r < 4; ++r) {
+                    const double xr = G[2 * (r * 4 + a)], xi = G[2 * (r * 4 + a) + 1];
+                    const double yr = G[2 * (r * 4 + b)], yi = G[2 * (r * 4 + b) + 1];
+                    re += xr * yr + xi * yi;
+                    im += xr * yi - xi * yr;
+                }
+                dev2 += re * re + im * im;
+                if (ctx->structure == 1 && ((__builtin_popcount(a) ^ __builtin_popcount(b)) & 1))
+                    off = std::max(off, std::hypot(G[2 * (a * 4 + b)], G[2 * (a * 4 + b) + 1]));
+            }
+        if (std::sqrt(dev2) > 1e-10)
+            return fail(ctx, RQ_EINVAL, "gate %d is not unitary: ||G^H G - I||_F = %.3e", p, std::sqrt(dev2));
+        if (off > 1e-10)
+            return fail(ctx, RQ_EINVAL, "parity gate %d has an entry of size %.3e outside the parity pattern", p, off);
+    }
+    return RQ_OK;
+}
+
+rq_status check_gates_device(rq_ctx *ctx, const double *d_gates) {
+    if (!ctx->checks) return RQ_OK;
+    if (!d_gates) return RQ_OK;  // the entry point reports the NULL
+    std::vector<double> h((size_t)ctx->P * 32);
+    RQ_CUDA(cudaMemcpyAsync(h.data(), d_gates, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    RQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    return check_gates(ctx, h.data());
+}
+
 // Host-memory evaluation shared by the host entry points and the trust
 // region: inputs are copied in, outputs copied out, then the stream is
 // synchronised.
@@ -795,14 +936,78 @@ rq_status eval_host(rq_ctx *ctx, const double *gates, const double *dirs, int k,
     if (!gates) return fail(ctx, RQ_EINVAL, "gates is NULL");
     if (k < 0) return fail(ctx, RQ_EINVAL, "k = %d < 0", k);
     if (k > 0 && !dirs) return fail(ctx, RQ_EINVAL, "dirs is NULL with k = %d", k);
+    RQ_TRY(check_gates(ctx, gates));
     RQ_TRY(ensure_small(ctx, k));
     cudaStream_t s = ctx->stream;
     const long long gsz = (long long)ctx->P * 32;
     RQ_CUDA(cudaMemcpyAsync(ctx->d_in_gates, gates, sizeof(double) * gsz, cudaMemcpyHostToDevice, s));
     if (k > 0) RQ_CUDA(cudaMemcpyAsync(ctx->d_dirs_raw, dirs, sizeof(double) * gsz * k, cudaMemcpyHostToDevice, s));
     double *o_f = ctx->d_out, *o_g = ctx->d_out + 2, *o_h = ctx->d_out + 2 + gsz;
-    RQ_TRY(eval_dev(ctx, reinterpret_cast<const double *>(ctx->d_in_gates),
-                    reinterpret_cast<const double *>(ctx->d_dirs_raw), k, want_env, o_f, o_g, o_h));
+    const double *i_g = reinterpret_cast<const double *>(ctx->d_in_gates);
+    const double *i_d = reinterpret_cast<const double *>(ctx->d_dirs_raw);
+    if (ctx->use_graphs && !ctx->prof_on) {
+        // the whole evaluation is captured once per (k, env_mode) and replayed
+        // as one graph launch while the configuration is unchanged
+        rq_ctx::GraphEntry *hit = nullptr;
+        for (auto &e : ctx->graphs) {
+            if (e.exec && e.version != ctx->version) {
+                cudaGraphExecDestroy(e.exec);
+                e = rq_ctx::GraphEntry{};
+            }
+            if (e.exec && e.k == k && e.env == want_env) hit = &e;
+        }
+        if (!hit) {
+            rq_ctx::GraphEntry *slot = nullptr;
+            for (auto &e : ctx->graphs)
+                if (!e.exec) slot = &e;
+            if (!slot && ctx->graphs.size() < 4) {
+                ctx->graphs.emplace_back();
+                slot = &ctx->graphs.back();
+            }
+            if (!slot) {  // evict the least recently used entry
+                slot = &ctx->graphs[0];
+                for (auto &e : ctx->graphs)
+                    if (e.last_use < slot->last_use) slot = &e;
+                cudaGraphExecDestroy(slot->exec);
+                *slot = rq_ctx::GraphEntry{};
+            }
+            const long long before = ctx->launches;
+            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                // a stream that cannot be captured (the legacy default stream,
+                // or one already capturing): launch directly from now on
+                cudaGetLastError();
+                ctx->use_graphs = false;
+                RQ_TRY(eval_dev(ctx, i_g, i_d, k, want_env, o_f, o_g, o_h));
+                goto copy_out;
+            }
+            const rq_status st = eval_dev(ctx, i_g, i_d, k, want_env, o_f, o_g, o_h);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+            if (st != RQ_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            if (ce != cudaSuccess) return fail(ctx, RQ_ECUDA, "evaluation capture: %s", cudaGetErrorString(ce));
+            const cudaError_t ie = cudaGraphInstantiate(&slot->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) {
+                slot->exec = nullptr;
+                return fail(ctx, RQ_ECUDA, "graph instantiation: %s", cudaGetErrorString(ie));
+            }
+            slot->k = k;
+            slot->env = want_env;
+            slot->version = ctx->version;
+            slot->launches = ctx->launches - before;
+            ctx->launches = before;  // captured, not yet launched
+            hit = slot;
+        }
+        hit->last_use = ++ctx->graph_clock;
+        RQ_CUDA(cudaGraphLaunch(hit->exec, s));
+        ctx->launches += hit->launches;
+    } else {
+        RQ_TRY(eval_dev(ctx, i_g, i_d, k, want_env, o_f, o_g, o_h));
+    }
+copy_out:
     if (f) RQ_CUDA(cudaMemcpyAsync(f, o_f, sizeof(double), cudaMemcpyDeviceToHost, s));
     if (rgrad && want_env == 1) RQ_CUDA(cudaMemcpyAsync(rgrad, o_g, sizeof(double) * gsz, cudaMemcpyDeviceToHost, s));
     if (hvps && k > 0) RQ_CUDA(cudaMemcpyAsync(hvps, o_h, sizeof(double) * gsz * k, cudaMemcpyDeviceToHost, s));
@@ -893,14 +1098,25 @@ rq_status rq_destroy(rq_ctx *ctx) {
 rq_status rq_setup_target(rq_ctx *ctx, const rq_target *tgt, const rq_circuit *c) {
     if (!ctx) return RQ_EINVAL;
     if (!tgt || !c) return fail(ctx, RQ_EINVAL, "target or circuit is NULL");
-    if (tgt->model != 0 && tgt->model != 1)
-        return fail(ctx, RQ_EINVAL, "model %d not supported (0 spinful, 1 spinless Fermi-Hubbard)", tgt->model);
-    const int per_site = tgt->model == 0 ? 2 : 1;
-    if (tgt->n_sites < 1 || per_site * tgt->n_sites != c->n_qubits || c->n_qubits < 2 || c->n_qubits > rq::kMaxQubits)
-        return fail(ctx, RQ_EINVAL, "n_qubits %d must equal %d * n_sites (%d), be >= 2 and <= %d", c->n_qubits,
-                    per_site, tgt->n_sites, rq::kMaxQubits);
-    if (!std::isfinite(tgt->J) || !std::isfinite(tgt->U) || !std::isfinite(tgt->t))
-        return fail(ctx, RQ_EINVAL, "J, U, t must be finite");
+    if (tgt->model < 0 || tgt->model > 2)
+        return fail(ctx, RQ_EINVAL, "model %d not supported (0 spinful, 1 spinless Fermi-Hubbard, 2 dense)",
+                    tgt->model);
+    if (tgt->model == 2) {
+        if (!tgt->dense_U) return fail(ctx, RQ_EINVAL, "model 2 needs dense_U");
+        if (c->n_qubits < 2 || c->n_qubits > rq::kMaxDenseQubits)
+            return fail(ctx, RQ_EINVAL, "model 2: n_qubits %d must be in [2, %d]", c->n_qubits, rq::kMaxDenseQubits);
+        const long long entries = 2LL << (2 * c->n_qubits);
+        for (long long i = 0; i < entries; ++i)
+            if (!std::isfinite(tgt->dense_U[i])) return fail(ctx, RQ_EINVAL, "dense_U has a non-finite entry");
+    } else {
+        const int per_site = tgt->model == 0 ? 2 : 1;
+        if (tgt->n_sites < 1 || per_site * tgt->n_sites != c->n_qubits || c->n_qubits < 2 ||
+            c->n_qubits > rq::kMaxQubits)
+            return fail(ctx, RQ_EINVAL, "n_qubits %d must equal %d * n_sites (%d), be >= 2 and <= %d", c->n_qubits,
+                        per_site, tgt->n_sites, rq::kMaxQubits);
+        if (!std::isfinite(tgt->J) || !std::isfinite(tgt->U) || !std::isfinite(tgt->t))
+            return fail(ctx, RQ_EINVAL, "J, U, t must be finite");
+    }
     if (c->n_gates < 1 || !c->pairs) return fail(ctx, RQ_EINVAL, "circuit needs n_gates >= 1 and pairs");
     if (c->structure != 0 && c->structure != 1) return fail(ctx, RQ_EINVAL, "structure must be 0 or 1");
     const int P = c->param_of ? c->n_params : c->n_gates;
@@ -915,8 +1131,9 @@ rq_status rq_setup_target(rq_ctx *ctx, const rq_target *tgt, const rq_circuit *c
     RQ_CUDA(cudaSetDevice(ctx->device));
     free_problem(ctx);
     ctx->tgt = *tgt;
+    ctx->tgt.dense_U = nullptr;  // copied into the device blocks below; the caller keeps ownership
     ctx->n = c->n_qubits;
-    ctx->L = tgt->n_sites;
+    ctx->L = tgt->model == 2 ? 0 : tgt->n_sites;
     ctx->g = c->n_gates;
     ctx->P = P;
     ctx->structure = c->structure;
@@ -942,7 +1159,7 @@ rq_status rq_setup_target(rq_ctx *ctx, const rq_target *tgt, const rq_circuit *c
             gg.qfirst = a != 0 ? 1 : 0;
         }
     }
-    rq_status st = build_target(ctx);
+    rq_status st = tgt->model == 2 ? build_target_dense(ctx, tgt->dense_U) : build_target(ctx);
     if (st != RQ_OK) {
         free_problem(ctx);
         return st;
@@ -1003,6 +1220,7 @@ rq_status rq_hessian(rq_ctx *ctx, const double *gates, double *f, double *egrad,
     if (ctx->ckpt_r != 1)
         return fail(ctx, RQ_EINVAL, "the full Hessian keeps every state, but the workspace keeps one every %d "
                     "gates: set the checkpoint interval to 1 (a smaller tile if memory is short)", ctx->ckpt_r);
+    RQ_TRY(rq::check_gates(ctx, gates));
     RQ_TRY(ensure_small(ctx, 1));
     cudaStream_t s = ctx->stream;
     const int g = ctx->g, P = ctx->P, B = ctx->B;
@@ -1180,7 +1398,8 @@ rq_status rq_set_translation(rq_ctx *ctx, int shift_sites) {
     }
     if (shift_sites < 0 || shift_sites >= L || L % shift_sites != 0)
         return fail(ctx, RQ_EINVAL, "shift %d must divide the %d sites and be smaller", shift_sites, L);
-    if (!ctx->tgt.periodic) return fail(ctx, RQ_EINVAL, "translation symmetry needs a periodic chain");
+    if (ctx->tgt.model == 2 || !ctx->tgt.periodic)
+        return fail(ctx, RQ_EINVAL, "translation symmetry needs a periodic chain model");
     // qubit map of the shift: site j -> j + s (mod L) on every chain
     std::vector<int> qmap(n);
     for (int q = 0; q < n; ++q) qmap[q] = (q < L) ? (q + shift_sites) % L : L + (q - L + shift_sites) % L;
@@ -1241,11 +1460,26 @@ rq_status rq_set_checkpointing(rq_ctx *ctx, int interval) {
     return rebuild_tiles(ctx);
 }
 
+rq_status rq_set_checks(rq_ctx *ctx, int enable) {
+    if (!ctx) return RQ_EINVAL;
+    ctx->checks = enable != 0;
+    return RQ_OK;
+}
+
+rq_status rq_set_graphs(rq_ctx *ctx, int enable) {
+    if (!ctx) return RQ_EINVAL;
+    RQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    drop_graphs(ctx);
+    ctx->use_graphs = enable != 0;
+    return RQ_OK;
+}
+
 rq_status rq_set_arithmetic(rq_ctx *ctx, int arith) {
     if (!ctx) return RQ_EINVAL;
     if (arith != RQ_ARITH_FP64 && arith != RQ_ARITH_DF64)
         return fail(ctx, RQ_EINVAL, "arithmetic %d is neither RQ_ARITH_FP64 nor RQ_ARITH_DF64", arith);
     ctx->arith = arith;
+    ++ctx->version;
     return RQ_OK;
 }
 
@@ -1254,6 +1488,7 @@ rq_status rq_set_gradient_space(rq_ctx *ctx, int space) {
     if (space != RQ_SPACE_RIEMANNIAN && space != RQ_SPACE_EUCLIDEAN)
         return fail(ctx, RQ_EINVAL, "space %d is neither RQ_SPACE_RIEMANNIAN nor RQ_SPACE_EUCLIDEAN", space);
     ctx->space = space;
+    ++ctx->version;
     return RQ_OK;
 }
 
@@ -1275,17 +1510,20 @@ rq_status rq_hvp(rq_ctx *ctx, const double *gates, const double *dirs, int k, do
 
 rq_status rq_cost_dev(rq_ctx *ctx, const double *gates, double *f) {
     if (!ctx) return RQ_EINVAL;
+    RQ_TRY(rq::check_gates_device(ctx, gates));
     return eval_dev(ctx, gates, nullptr, 0, 0, f, nullptr, nullptr);
 }
 
 rq_status rq_grad_dev(rq_ctx *ctx, const double *gates, double *f, double *rgrad) {
     if (!ctx) return RQ_EINVAL;
+    RQ_TRY(rq::check_gates_device(ctx, gates));
     return eval_dev(ctx, gates, nullptr, 0, 1, f, rgrad, nullptr);
 }
 
 rq_status rq_hvp_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, double *f, double *rgrad,
                      double *hvps) {
     if (!ctx) return RQ_EINVAL;
+    RQ_TRY(rq::check_gates_device(ctx, gates));
     return eval_dev(ctx, gates, dirs, k, 1, f, rgrad, hvps);
 }
 
@@ -1332,6 +1570,7 @@ rq_status rq_profile_start(rq_ctx *ctx) {
     if (!ctx) return RQ_EINVAL;
     ctx->prof_on = true;
     ctx->prof_used = 0;
+    ++ctx->version;
     return RQ_OK;
 }
 

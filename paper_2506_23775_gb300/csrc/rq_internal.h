@@ -15,6 +15,7 @@ constexpr int kThreads = 256;      // threads per CTA of every sweep kernel
 constexpr int kCtasPerSm = 2;      // sweep CTAs launched per SM (grid size)
 constexpr int kMaxDirs = 4;        // HVP directions swept together
 constexpr int kMaxQubits = 20;
+constexpr int kMaxDenseQubits = 14;  // dense targets: 2^28 complex entries at most
 constexpr int kEnvDoubles = 32;    // one 4x4 complex environment
 
 // Which kernel family handles a gate.
@@ -129,6 +130,8 @@ void launch_geometry(const double2 *gates, const double2 *dirs, const double *en
 rq_status eval_host(rq_ctx *ctx, const double *gates, const double *dirs, int k, int want_env, double *f,
                     double *rgrad, double *hvps);
 rq_status set_error(rq_ctx *ctx, rq_status code, const char *msg);
+rq_status check_gates(rq_ctx *ctx, const double *gates);
+rq_status check_gates_device(rq_ctx *ctx, const double *d_gates);
 int gradient_space(const rq_ctx *ctx);
 // Device-pointer evaluation on the context stream (capturable once the
 // context's small buffers hold k directions: prepare_capacity first).

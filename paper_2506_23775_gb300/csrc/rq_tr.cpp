@@ -172,9 +172,11 @@ extern "C" rq_status rq_tr_step(rq_ctx *ctx, double *gates, rq_tr_state *st) {
     struct SpaceGuard {
         rq_ctx *c;
         int saved;
-        ~SpaceGuard() { rq_set_gradient_space(c, saved); }
+        ~SpaceGuard() {
+            if (saved != RQ_SPACE_RIEMANNIAN) rq_set_gradient_space(c, saved);
+        }
     } guard{ctx, rq::gradient_space(ctx)};
-    rq_set_gradient_space(ctx, RQ_SPACE_RIEMANNIAN);
+    if (guard.saved != RQ_SPACE_RIEMANNIAN) rq_set_gradient_space(ctx, RQ_SPACE_RIEMANNIAN);
     const size_t dimv = (size_t)P * 32;
     const int dim = P * (info.structure == 1 ? 8 : 16);
     const int max_inner = st->max_inner > 0 ? st->max_inner : dim;

@@ -25,7 +25,7 @@ EXPORTS = ("rq_create", "rq_destroy", "rq_setup_target", "rq_set_columns", "rq_s
            "rq_cost_static", "rq_set_gradient_space", "rq_batch_create", "rq_batch_destroy",
            "rq_batch_add", "rq_batch_set_tile", "rq_batch_hvp", "rq_batch_info", "rq_batch_last_error",
            "rq_set_arithmetic", "rq_set_translation", "rq_hessian", "rq_set_checkpointing",
-           "rq_last_error")
+           "rq_set_graphs", "rq_set_checks", "rq_last_error")
 
 
 class RQCircuit(C.Structure):
@@ -36,7 +36,8 @@ class RQCircuit(C.Structure):
 
 class RQTarget(C.Structure):
     _fields_ = [("model", C.c_int), ("n_sites", C.c_int), ("periodic", C.c_int),
-                ("J", C.c_double), ("U", C.c_double), ("t", C.c_double)]
+                ("J", C.c_double), ("U", C.c_double), ("t", C.c_double),
+                ("dense_U", C.POINTER(C.c_double))]
 
 
 class RQTRState(C.Structure):
@@ -98,6 +99,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "rq_set_translation": ([vp, C.c_int], C.c_int),
         "rq_hessian": ([vp, dp, dp, dp, dp], C.c_int),
         "rq_set_checkpointing": ([vp, C.c_int], C.c_int),
+        "rq_set_graphs": ([vp, C.c_int], C.c_int),
+        "rq_set_checks": ([vp, C.c_int], C.c_int),
         "rq_batch_create": ([C.POINTER(vp), C.c_int], C.c_int),
         "rq_batch_destroy": ([vp], C.c_int),
         "rq_batch_add": ([vp, C.POINTER(RQTarget), C.POINTER(RQCircuit), C.POINTER(C.c_int)], C.c_int),
@@ -165,7 +168,10 @@ class Context:
     # --- set-up ---------------------------------------------------------
     def setup(self, n_sites: int, pairs, param_of=None, n_params: Optional[int] = None,
               structure: int = 0, J: float = 1.0, U: float = 4.0, t: float = 0.5,
-              periodic: bool = False, model: int = 0):
+              periodic: bool = False, model: int = 0, dense_U=None, n_qubits: Optional[int] = None):
+        """Chain targets (model 0 spinful, 1 spinless) from (n_sites, J, U, t,
+        periodic); model 2 takes a dense ``dense_U`` (2^n x 2^n complex) and
+        ``n_qubits`` instead."""
         pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
         self._pairs = pairs
         if param_of is not None:
@@ -176,10 +182,18 @@ class Context:
             self._param_of = None
             npar = pairs.shape[0]
             pp = None
-        nq = (2 if model == 0 else 1) * n_sites
+        dptr = None
+        if model == 2:
+            dense = np.ascontiguousarray(dense_U, dtype=np.complex128)
+            nq = int(n_qubits) if n_qubits is not None else int(round(np.log2(dense.shape[0])))
+            if dense.shape != (1 << nq, 1 << nq):
+                raise ValueError(f"dense_U must be {1 << nq} x {1 << nq}, got {dense.shape}")
+            dptr = dense.ctypes.data_as(C.POINTER(C.c_double))
+        else:
+            nq = (2 if model == 0 else 1) * n_sites
         circ = RQCircuit(nq, pairs.shape[0], npar, structure,
                          pairs.ctypes.data_as(C.POINTER(C.c_int32)), pp)
-        tgt = RQTarget(model, n_sites, 1 if periodic else 0, J, U, t)
+        tgt = RQTarget(model, n_sites, 1 if periodic else 0, J, U, t, dptr)
         self._check(self._lib.rq_setup_target(self._h, C.byref(tgt), C.byref(circ)))
         self.n_params, self.n_qubits, self.structure = npar, nq, structure
         return self
@@ -202,6 +216,14 @@ class Context:
         """Keep the forward state every ``interval`` gates (1: every gate) and
         recompute the rest in the backward pass."""
         self._check(self._lib.rq_set_checkpointing(self._h, int(interval)))
+
+    def set_checks(self, enable: bool):
+        """Validate the gates of every call (unitarity, parity pattern)."""
+        self._check(self._lib.rq_set_checks(self._h, 1 if enable else 0))
+
+    def set_graphs(self, enable: bool):
+        """Capture host-memory evaluations into CUDA graphs (default on)."""
+        self._check(self._lib.rq_set_graphs(self._h, 1 if enable else 0))
 
     def set_translation(self, shift_sites: int):
         """Sum over translation-orbit representatives (0: plain basis sums)."""

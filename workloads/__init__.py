@@ -16,6 +16,7 @@ from .fermi_hubbard import (  # noqa: F401
     parity_mask,
     make_problem,
     random_directions,
+    random_unitary,
     config_problem,
     batch_problems,
     make_spinless_problem,

@@ -214,6 +214,17 @@ def random_directions(n_params: int, k: int, seed: int) -> np.ndarray:
             + 1j * rng.standard_normal((k, n_params, 4, 4)))
 
 
+def random_unitary(dim: int, seed: int) -> np.ndarray:
+    """Haar-distributed ``dim x dim`` unitary (QR of a complex Gaussian
+    matrix with the phases of R's diagonal moved into Q), a dense target for
+    tests of targets that are not a chain's time evolution."""
+    rng = np.random.default_rng(seed)
+    z = (rng.standard_normal((dim, dim)) + 1j * rng.standard_normal((dim, dim))) / np.sqrt(2.0)
+    q, r = np.linalg.qr(z)
+    d = np.diagonal(r)
+    return q * (d / np.abs(d))
+
+
 # Spinless chain (paper Eq. slFH_qubit) -----------------------------------------
 
 def spinless_layers(L: int, depth: int, periodic: bool = False):
