@@ -101,6 +101,7 @@ struct rq_ctx {
     bool use_graphs = true;
     long long version = 0, graph_clock = 0;
     int checks = 0;  // validate the gates of every call (unitarity, parity pattern)
+    bool first_layer = true;  // FP64 sweeps of the leading disjoint gates visit only nonzero items
 };
 
 namespace {
@@ -689,6 +690,7 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
             RQ_LAUNCHED();
         }
     }
+    const bool first_layer = ctx->first_layer && !df;  // the df64 kernels sweep every item
     const double2 *gsrc = df ? ctx->d_gates_df : ctx->d_gates;
     const double2 *dsrc = df ? ctx->d_dirs_df : ctx->d_dirs;
     const int B = ctx->B;
@@ -728,6 +730,15 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                 a.log2B = ctx->log2B;
                 a.tile_parity = par;
                 a.n_items = (geo.mode == rq::kParity2 ? ctx->n_store / 2 : ctx->n_store / 4) * B;
+                if (geo.restricted && first_layer) {
+                    // only the items where psi_{l-1} can be nonzero; the rest
+                    // of psi_l (and its tangents) is zero
+                    a.cols = cols;
+                    a.n_items = (long long)B << __builtin_popcountll(geo.free_bits);
+                    RQ_CUDA(cudaMemsetAsync(a.psi_out, 0, sizeof(double2) * tile, s));
+                    for (int d = 0; d < kd; ++d)
+                        RQ_CUDA(cudaMemsetAsync(a.dpsi_out + d * set, 0, sizeof(double2) * tile, s));
+                }
                 {
                     const double amps = geo.mode == rq::kParity2 ? 2.0 : 4.0;
                     const double cm = geo.mode == rq::kGeneral ? 16.0 : (geo.mode == rq::kParity4 ? 8.0 : 4.0);
@@ -806,6 +817,12 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                 a.tile_parity = par;
                 a.update = l > 0 ? 1 : 0;
                 a.n_items = (geo.mode == rq::kParity2 ? ctx->n_store / 2 : ctx->n_store / 4) * B;
+                if (geo.restricted && first_layer) {
+                    // E_l needs only the items where psi_{l-1} can be nonzero,
+                    // and lambda_{l-1} is read only there by the earlier gates
+                    a.cols = cols;
+                    a.n_items = (long long)B << __builtin_popcountll(geo.free_bits);
+                }
                 for (int d = 0; d < kd; ++d) {
                     rq::BwdArgs b = a;
                     b.dlam = ctx->d_dlam + d * tile;
@@ -1159,6 +1176,22 @@ rq_status rq_setup_target(rq_ctx *ctx, const rq_target *tgt, const rq_circuit *c
             gg.qfirst = a != 0 ? 1 : 0;
         }
     }
+    // The leading run of pairwise disjoint general gates acts on a basis
+    // state: before gate l of the run only the qubits of the earlier gates of
+    // the run can differ from the column's basis state.
+    if (ctx->structure == 0) {
+        const long long all = ctx->n_store - 1;
+        long long used = 0;
+        for (int l = 0; l < ctx->g; ++l) {
+            GateGeom &gg = ctx->geo[l];
+            const long long bits = (1LL << gg.pa) | (1LL << gg.pb);
+            if (used & bits) break;
+            gg.free_bits = used;
+            used |= bits;
+            gg.fixed_bits = all & ~used;
+            gg.restricted = gg.fixed_bits != 0;
+        }
+    }
     rq_status st = tgt->model == 2 ? build_target_dense(ctx, tgt->dense_U) : build_target(ctx);
     if (st != RQ_OK) {
         free_problem(ctx);
@@ -1458,6 +1491,13 @@ rq_status rq_set_checkpointing(rq_ctx *ctx, int interval) {
     if (interval < 0) return fail(ctx, RQ_EINVAL, "checkpoint interval %d < 0", interval);
     ctx->ckpt_req = interval;
     return rebuild_tiles(ctx);
+}
+
+rq_status rq_set_first_layer(rq_ctx *ctx, int enable) {
+    if (!ctx) return RQ_EINVAL;
+    ctx->first_layer = enable != 0;
+    ++ctx->version;
+    return RQ_OK;
 }
 
 rq_status rq_set_checks(rq_ctx *ctx, int enable) {

@@ -30,6 +30,13 @@ struct GateGeom {
     int pa, pb;    // stored bit positions of the listed qubits (kParity2: pa = other qubit, pb = -1)
     int qfirst;    // kParity2: 1 if the stored qubit is listed first
     int param;     // parameter gate index
+    // First-layer support (general gates of the leading run of disjoint
+    // gates): psi_{l-1} of column j is zero unless the stored bits in
+    // fixed_bits equal those of j, so a sweep of gate l visits only the items
+    // whose free_bits (the qubits of the earlier gates of the run) take every
+    // value.  restricted = 0: every item.
+    int restricted = 0;
+    long long free_bits = 0, fixed_bits = 0;
 };
 
 // Arguments of one forward gate step over a tile.
@@ -47,6 +54,7 @@ struct FwdArgs {
     int log2B;
     int tile_parity;
     long long n_items;
+    const int32_t *cols = nullptr;  // column basis states (-1: padding) when geo.restricted
 };
 
 // Arguments of one backward gate step over a tile.
@@ -64,6 +72,7 @@ struct BwdArgs {
     int accumulate;             // base step: 0 skips the environment (and part)
     long long n_items;
     double *part;               // [gridDim.x][32] per-CTA partial environments
+    const int32_t *cols = nullptr;  // column basis states (-1: padding) when geo.restricted
 };
 
 // Sector tables of the stored target.

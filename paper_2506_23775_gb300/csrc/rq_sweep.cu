@@ -25,9 +25,30 @@
 //   gate on qubit 0 acts as one 2x2 block on two stored amplitudes, the block
 //   chosen by the parity of the other stored bits.
 //
+// * First-layer support: a sweep starts from a basis state |j>, so before
+//   gate l of the leading run of pairwise disjoint gates psi is |j> on every
+//   qubit outside the run's earlier gates.  For those general gates an item
+//   index enumerates only the free bits and takes the fixed ones from j; the
+//   forward output outside that set is zero (cleared before the launch) and
+//   the backward pass needs lambda_{l-1} only on it (the earlier gates of the
+//   run read a subset).
+//
 // Environments are accumulated per thread in FP64 registers, reduced with a
 // fixed warp-shuffle tree and a fixed-order block sum into one partial per
 // CTA; a later kernel sums the partials in CTA order (deterministic).
+//
+// General gates use three real multiply-adds per complex product instead of
+// four (Gauss's three-multiplication form): for m = a + ib and x = u + iv,
+//   m x = (k - b (u + v)) + i (k + a (v - u)),  k = u (a + b),
+// with a + b tabulated once per gate (in shared memory) and u + v, v - u
+// formed once per amplitude and reused by every output and environment entry
+// that amplitude meets.  The environment entry conj(l) x, l = p + iq, is kept
+// as three sums, K1 = sum u (p - q), K2 = sum p (v - u), K3 = sum q (u + v),
+// with Re = K1 + K3 and Im = K1 + K2 formed once per thread before the block
+// reduction.  GB300's FP64 pipe is the bound of these kernels, and this cuts
+// the FP64 instructions of a general-gate item by 12.5-17 %; the parity-gate
+// paths touch two entries per row, where the per-amplitude sums cost as much
+// as they save, so they keep the four-product form.
 #include "rq_internal.h"
 
 namespace rq {
@@ -56,18 +77,148 @@ __device__ __forceinline__ void cmacc(double2 &acc, const double2 a, const doubl
 
 __device__ __forceinline__ double2 zero2() { return make_double2(0.0, 0.0); }
 
-// Stored offsets of the four amplitudes of item (r, b) for a gate on the
-// listed pair with stored bit positions pa (first listed) and pb.
-__device__ __forceinline__ void offsets4(long long r, long long b, int pa, int pb, int log2B,
-                                         long long (&off)[4]) {
-    const int plo = pa < pb ? pa : pb;
-    const int phi = pa < pb ? pb : pa;
-    const long long x0 = insert_zero(insert_zero(r, plo), phi);
+// A general 4x4 complex matrix tabulated for the three-product form:
+// s = a + b, a, nb = -b of each entry m = a + ib, row-major.
+struct Mat3 {
+    double s[16], a[16], nb[16];
+};
+
+// Tabulate G (adjoint = 0) or G^dagger (adjoint = 1) from 16 complex entries;
+// called by threads 0..15, entry e each.
+__device__ __forceinline__ void tabulate3(Mat3 &m, const double2 *g, int e, int adjoint) {
+    const int r = e >> 2, c = e & 3;
+    double re, im;
+    if (adjoint) {  // (G^dagger)[r][c] = conj(G[c][r])
+        re = g[c * 4 + r].x;
+        im = -g[c * 4 + r].y;
+    } else {
+        re = g[e].x;
+        im = g[e].y;
+    }
+    m.s[e] = re + im;
+    m.a[e] = re;
+    m.nb[e] = -im;
+}
+
+// An amplitude x = u + iv with its sums: u, S = u + v, D = v - u (and v).
+struct Amp3 {
+    double u, v, S, D;
+};
+
+__device__ __forceinline__ Amp3 amp3(const double2 x) {
+    Amp3 r;
+    r.u = x.x;
+    r.v = x.y;
+    r.S = x.x + x.y;
+    r.D = x.y - x.x;
+    return r;
+}
+
+// y_i = sum_c M[i][c] x_c for the four outputs (three products per term).
+__device__ __forceinline__ void matvec3(const Mat3 &m, const Amp3 (&x)[4], double2 (&y)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        double k = x[0].u * m.s[i * 4];
+#pragma unroll
+        for (int c = 1; c < 4; ++c) k = fma(x[c].u, m.s[i * 4 + c], k);
+        double re = k, im = k;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            re = fma(m.nb[i * 4 + c], x[c].S, re);
+            im = fma(m.a[i * 4 + c], x[c].D, im);
+        }
+        y[i] = make_double2(re, im);
+    }
+}
+
+// y_i = sum_c M[i][c] x_c + N[i][c] w_c (a tangent step).
+__device__ __forceinline__ void matvec3_pair(const Mat3 &m, const Amp3 (&x)[4], const Mat3 &n,
+                                             const Amp3 (&w)[4], double2 (&y)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        double k = x[0].u * m.s[i * 4];
+#pragma unroll
+        for (int c = 1; c < 4; ++c) k = fma(x[c].u, m.s[i * 4 + c], k);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) k = fma(w[c].u, n.s[i * 4 + c], k);
+        double re = k, im = k;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            re = fma(m.nb[i * 4 + c], x[c].S, re);
+            im = fma(m.a[i * 4 + c], x[c].D, im);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            re = fma(n.nb[i * 4 + c], w[c].S, re);
+            im = fma(n.a[i * 4 + c], w[c].D, im);
+        }
+        y[i] = make_double2(re, im);
+    }
+}
+
+// Environment sums of conj(l_i) x_c over all 16 (i, c): K1 += u_c (p_i - q_i)
+// (p - q = -D of l), K2 += p_i D_c, K3 += q_i S_c.
+__device__ __forceinline__ void env3(double (&K1)[16], double (&K2)[16], double (&K3)[16], const Amp3 (&l)[4],
+                                     const Amp3 (&x)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            K1[i * 4 + c] = fma(-l[i].D, x[c].u, K1[i * 4 + c]);
+            K2[i * 4 + c] = fma(l[i].u, x[c].D, K2[i * 4 + c]);
+            K3[i * 4 + c] = fma(l[i].v, x[c].S, K3[i * 4 + c]);
+        }
+}
+
+// E[i] = (K1 + K3, K1 + K2)
+__device__ __forceinline__ void env3_finish(const double (&K1)[16], const double (&K2)[16], const double (&K3)[16],
+                                            double2 (&E)[16]) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) E[i] = make_double2(K1[i] + K3[i], K1[i] + K2[i]);
+}
+
+// Stored offsets of the four amplitudes of an item whose amplitude with both
+// gate bits clear is x0, for a gate on stored bits pa (first listed) and pb.
+__device__ __forceinline__ void offsets4_at(long long x0, long long b, int pa, int pb, int log2B,
+                                            long long (&off)[4]) {
     const long long sa = 1LL << pa, sb = 1LL << pb;
     off[0] = (x0 << log2B) | b;
     off[1] = ((x0 | sb) << log2B) | b;
     off[2] = ((x0 | sa) << log2B) | b;
     off[3] = ((x0 | sa | sb) << log2B) | b;
+}
+
+// ... of item (r, b): r enumerates the other n - 2 stored bits.
+__device__ __forceinline__ void offsets4(long long r, long long b, int pa, int pb, int log2B,
+                                         long long (&off)[4]) {
+    const int plo = pa < pb ? pa : pb;
+    const int phi = pa < pb ? pb : pa;
+    offsets4_at(insert_zero(insert_zero(r, plo), phi), b, pa, pb, log2B, off);
+}
+
+// The low bits of t placed, in order, at the set bits of mask.
+__device__ __forceinline__ long long deposit_bits(long long t, long long mask) {
+    long long out = 0;
+    for (long long m = mask; m != 0; m &= m - 1, t >>= 1)
+        if (t & 1) out |= m & -m;
+    return out;
+}
+
+// Offsets of item (t, b) of a general gate.  Unrestricted: t = r.  A gate of
+// the leading run of disjoint gates (geo.restricted, with the tile's columns):
+// t enumerates only the free bits, the fixed bits are those of column b's
+// basis state, where psi_{l-1} can be nonzero.  Returns false for a padding
+// column (nothing to do).
+__device__ __forceinline__ bool general_item(const GateGeom &geo, const int32_t *cols, long long t, long long b,
+                                             int log2B, long long (&off)[4]) {
+    if (cols != nullptr && geo.restricted) {
+        const int j = cols[b];
+        if (j < 0) return false;
+        offsets4_at(deposit_bits(t, geo.free_bits) | ((long long)j & geo.fixed_bits), b, geo.pa, geo.pb, log2B, off);
+        return true;
+    }
+    offsets4(t, b, geo.pa, geo.pb, log2B, off);
+    return true;
 }
 
 // kParity2 item: the two stored amplitudes differ in the stored qubit at
@@ -97,34 +248,53 @@ template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1) k_fwd(const FwdArgs a) {
     __shared__ double2 sg[16];
     __shared__ double2 sx[kMaxDirs][16];
-    if (threadIdx.x < 16) sg[threadIdx.x] = a.gate[threadIdx.x];
-    if (threadIdx.x < 16 * a.kdirs)
-        sx[threadIdx.x >> 4][threadIdx.x & 15] = a.dirs[(threadIdx.x >> 4) * a.xdir_stride + (threadIdx.x & 15)];
+    __shared__ Mat3 sg3;
+    __shared__ Mat3 sx3[kMaxDirs];
+    if (MODE == kGeneral) {
+        if (threadIdx.x < 16) tabulate3(sg3, a.gate, threadIdx.x, 0);
+        if (threadIdx.x < 16 * a.kdirs)
+            tabulate3(sx3[threadIdx.x >> 4], a.dirs + (threadIdx.x >> 4) * a.xdir_stride, threadIdx.x & 15, 0);
+    } else {
+        if (threadIdx.x < 16) sg[threadIdx.x] = a.gate[threadIdx.x];
+        if (threadIdx.x < 16 * a.kdirs)
+            sx[threadIdx.x >> 4][threadIdx.x & 15] = a.dirs[(threadIdx.x >> 4) * a.xdir_stride + (threadIdx.x & 15)];
+    }
     __syncthreads();
     const long long Bm = (1LL << a.log2B) - 1;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.n_items; it += stride) {
         const long long b = it & Bm, r = it >> a.log2B;
-        if (MODE == kGeneral || MODE == kParity4) {
+        if constexpr (MODE == kGeneral) {
+            long long off[4];
+            if (!general_item(a.geo, a.cols, r, b, a.log2B, off)) continue;
+            Amp3 x[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) x[c] = amp3(__ldg(&a.psi_in[off[c]]));
+            double2 q[4];
+            matvec3(sg3, x, q);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) a.psi_out[off[c]] = q[c];
+            for (int d = 0; d < a.kdirs; ++d) {
+                const double2 *din = a.dpsi_in + d * a.dir_stride;
+                double2 *dout = a.dpsi_out + d * a.dir_stride;
+                Amp3 t[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) t[c] = amp3(__ldg(&din[off[c]]));
+                matvec3_pair(sg3, t, sx3[d], x, q);  // G psi' + X psi
+#pragma unroll
+                for (int c = 0; c < 4; ++c) dout[off[c]] = q[c];
+            }
+        } else if constexpr (MODE == kParity4) {
             long long off[4];
             offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
             double2 p[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) p[c] = __ldg(&a.psi_in[off[c]]);
             double2 q[4];
-            if (MODE == kGeneral) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    q[i] = zero2();
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) cmac(q[i], sg[i * 4 + c], p[c]);
-                }
-            } else {
-                q[0] = zero2(); cmac(q[0], sg[0], p[0]); cmac(q[0], sg[3], p[3]);
-                q[3] = zero2(); cmac(q[3], sg[12], p[0]); cmac(q[3], sg[15], p[3]);
-                q[1] = zero2(); cmac(q[1], sg[5], p[1]); cmac(q[1], sg[6], p[2]);
-                q[2] = zero2(); cmac(q[2], sg[9], p[1]); cmac(q[2], sg[10], p[2]);
-            }
+            q[0] = zero2(); cmac(q[0], sg[0], p[0]); cmac(q[0], sg[3], p[3]);
+            q[3] = zero2(); cmac(q[3], sg[12], p[0]); cmac(q[3], sg[15], p[3]);
+            q[1] = zero2(); cmac(q[1], sg[5], p[1]); cmac(q[1], sg[6], p[2]);
+            q[2] = zero2(); cmac(q[2], sg[9], p[1]); cmac(q[2], sg[10], p[2]);
 #pragma unroll
             for (int c = 0; c < 4; ++c) a.psi_out[off[c]] = q[c];
             for (int d = 0; d < a.kdirs; ++d) {
@@ -133,29 +303,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_fwd(const FwdArgs a) {
                 double2 t[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) t[c] = __ldg(&din[off[c]]);
-                if (MODE == kGeneral) {
+                const int E0[2] = {0, 3}, O0[2] = {1, 2};
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        q[i] = zero2();
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            cmac(q[i], sg[i * 4 + c], t[c]);
-                            cmac(q[i], sx[d][i * 4 + c], p[c]);
-                        }
-                    }
-                } else {
-                    const int E0[2] = {0, 3}, O0[2] = {1, 2};
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const int i = E0[u];
-                        q[i] = zero2();
-                        cmac(q[i], sg[i * 4 + 0], t[0]); cmac(q[i], sg[i * 4 + 3], t[3]);
-                        cmac(q[i], sx[d][i * 4 + 0], p[0]); cmac(q[i], sx[d][i * 4 + 3], p[3]);
-                        const int o = O0[u];
-                        q[o] = zero2();
-                        cmac(q[o], sg[o * 4 + 1], t[1]); cmac(q[o], sg[o * 4 + 2], t[2]);
-                        cmac(q[o], sx[d][o * 4 + 1], p[1]); cmac(q[o], sx[d][o * 4 + 2], p[2]);
-                    }
+                for (int u = 0; u < 2; ++u) {
+                    const int i = E0[u];
+                    q[i] = zero2();
+                    cmac(q[i], sg[i * 4 + 0], t[0]); cmac(q[i], sg[i * 4 + 3], t[3]);
+                    cmac(q[i], sx[d][i * 4 + 0], p[0]); cmac(q[i], sx[d][i * 4 + 3], p[3]);
+                    const int o = O0[u];
+                    q[o] = zero2();
+                    cmac(q[o], sg[o * 4 + 1], t[1]); cmac(q[o], sg[o * 4 + 2], t[2]);
+                    cmac(q[o], sx[d][o * 4 + 1], p[1]); cmac(q[o], sx[d][o * 4 + 2], p[2]);
                 }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) dout[off[c]] = q[c];
@@ -222,16 +380,41 @@ template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1) k_bwd_base(const BwdArgs a) {
     const int accumulate = a.accumulate;
     __shared__ double2 sg[16];
-    if (threadIdx.x < 16) sg[threadIdx.x] = a.gate[threadIdx.x];
+    __shared__ Mat3 sgT3;  // G^dagger, general gates
+    if (threadIdx.x < 16) {
+        if (MODE == kGeneral) tabulate3(sgT3, a.gate, threadIdx.x, 1);
+        else sg[threadIdx.x] = a.gate[threadIdx.x];
+    }
     __syncthreads();
     double2 E[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) E[i] = zero2();
+    double K1[16], K2[16], K3[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) K1[i] = K2[i] = K3[i] = 0.0;
     const long long Bm = (1LL << a.log2B) - 1;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.n_items; it += stride) {
         const long long b = it & Bm, r = it >> a.log2B;
-        if (MODE == kGeneral || MODE == kParity4) {
+        if constexpr (MODE == kGeneral) {
+            long long off[4];
+            if (!general_item(a.geo, a.cols, r, b, a.log2B, off)) continue;
+            Amp3 l[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) l[c] = amp3(a.lam[off[c]]);
+            if (accumulate) {
+                Amp3 p[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) p[c] = amp3(__ldg(&a.psi[off[c]]));
+                env3(K1, K2, K3, l, p);
+            }
+            if (a.update) {
+                double2 q[4];
+                matvec3(sgT3, l, q);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) a.lam[off[c]] = q[c];
+            }
+        } else if constexpr (MODE == kParity4) {
             long long off[4];
             offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
             double2 l[4];
@@ -241,33 +424,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_base(const BwdArgs a) {
                 double2 p[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) p[c] = __ldg(&a.psi[off[c]]);
-                if (MODE == kGeneral) {
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) cmacc(E[i * 4 + c], l[i], p[c]);
-                } else {
-                    cmacc(E[0], l[0], p[0]); cmacc(E[3], l[0], p[3]);
-                    cmacc(E[12], l[3], p[0]); cmacc(E[15], l[3], p[3]);
-                    cmacc(E[5], l[1], p[1]); cmacc(E[6], l[1], p[2]);
-                    cmacc(E[9], l[2], p[1]); cmacc(E[10], l[2], p[2]);
-                }
+                cmacc(E[0], l[0], p[0]); cmacc(E[3], l[0], p[3]);
+                cmacc(E[12], l[3], p[0]); cmacc(E[15], l[3], p[3]);
+                cmacc(E[5], l[1], p[1]); cmacc(E[6], l[1], p[2]);
+                cmacc(E[9], l[2], p[1]); cmacc(E[10], l[2], p[2]);
             }
             if (a.update) {
                 double2 q[4];
-                if (MODE == kGeneral) {
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        q[i] = zero2();
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) cmacc(q[i], sg[c * 4 + i], l[c]);
-                    }
-                } else {
-                    q[0] = zero2(); cmacc(q[0], sg[0], l[0]); cmacc(q[0], sg[12], l[3]);
-                    q[3] = zero2(); cmacc(q[3], sg[3], l[0]); cmacc(q[3], sg[15], l[3]);
-                    q[1] = zero2(); cmacc(q[1], sg[5], l[1]); cmacc(q[1], sg[9], l[2]);
-                    q[2] = zero2(); cmacc(q[2], sg[6], l[1]); cmacc(q[2], sg[10], l[2]);
-                }
+                q[0] = zero2(); cmacc(q[0], sg[0], l[0]); cmacc(q[0], sg[12], l[3]);
+                q[3] = zero2(); cmacc(q[3], sg[3], l[0]); cmacc(q[3], sg[15], l[3]);
+                q[1] = zero2(); cmacc(q[1], sg[5], l[1]); cmacc(q[1], sg[9], l[2]);
+                q[2] = zero2(); cmacc(q[2], sg[6], l[1]); cmacc(q[2], sg[10], l[2]);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) a.lam[off[c]] = q[c];
             }
@@ -302,6 +469,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_base(const BwdArgs a) {
             }
         }
     }
+    if constexpr (MODE == kGeneral) env3_finish(K1, K2, K3, E);
     if (accumulate) block_reduce_store(E, a.part + (long long)blockIdx.x * kEnvDoubles);
 }
 
@@ -314,19 +482,47 @@ template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1) k_bwd_dir(const BwdArgs a) {
     __shared__ double2 sg[16];
     __shared__ double2 sx[16];
+    __shared__ Mat3 sgT3, sxT3;  // G^dagger, X^dagger, general gates
     if (threadIdx.x < 16) {
-        sg[threadIdx.x] = a.gate[threadIdx.x];
-        sx[threadIdx.x] = a.dir[threadIdx.x];
+        if (MODE == kGeneral) {
+            tabulate3(sgT3, a.gate, threadIdx.x, 1);
+            tabulate3(sxT3, a.dir, threadIdx.x, 1);
+        } else {
+            sg[threadIdx.x] = a.gate[threadIdx.x];
+            sx[threadIdx.x] = a.dir[threadIdx.x];
+        }
     }
     __syncthreads();
     double2 E[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) E[i] = zero2();
+    double K1[16], K2[16], K3[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) K1[i] = K2[i] = K3[i] = 0.0;
     const long long Bm = (1LL << a.log2B) - 1;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.n_items; it += stride) {
         const long long b = it & Bm, r = it >> a.log2B;
-        if (MODE == kGeneral || MODE == kParity4) {
+        if constexpr (MODE == kGeneral) {
+            long long off[4];
+            if (!general_item(a.geo, a.cols, r, b, a.log2B, off)) continue;
+            Amp3 l[4], dl[4], p[4], dp[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                l[c] = amp3(__ldg(&a.lam[off[c]]));
+                dl[c] = amp3(a.dlam[off[c]]);
+                p[c] = amp3(__ldg(&a.psi[off[c]]));
+                dp[c] = amp3(__ldg(&a.dpsi[off[c]]));
+            }
+            env3(K1, K2, K3, dl, p);
+            env3(K1, K2, K3, l, dp);
+            if (a.update) {
+                double2 q[4];
+                matvec3_pair(sgT3, dl, sxT3, l, q);  // G^dagger lambda' + X^dagger lambda
+#pragma unroll
+                for (int c = 0; c < 4; ++c) a.dlam[off[c]] = q[c];
+            }
+        } else if constexpr (MODE == kParity4) {
             long long off[4];
             offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
             double2 l[4], dl[4], p[4], dp[4];
@@ -337,44 +533,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_dir(const BwdArgs a) {
                 p[c] = __ldg(&a.psi[off[c]]);
                 dp[c] = __ldg(&a.dpsi[off[c]]);
             }
-            if (MODE == kGeneral) {
+            const int idx[8][2] = {{0, 0}, {0, 3}, {3, 0}, {3, 3}, {1, 1}, {1, 2}, {2, 1}, {2, 2}};
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        cmacc(E[i * 4 + c], dl[i], p[c]);
-                        cmacc(E[i * 4 + c], l[i], dp[c]);
-                    }
-            } else {
-                const int idx[8][2] = {{0, 0}, {0, 3}, {3, 0}, {3, 3}, {1, 1}, {1, 2}, {2, 1}, {2, 2}};
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    cmacc(E[idx[u][0] * 4 + idx[u][1]], dl[idx[u][0]], p[idx[u][1]]);
-                    cmacc(E[idx[u][0] * 4 + idx[u][1]], l[idx[u][0]], dp[idx[u][1]]);
-                }
+            for (int u = 0; u < 8; ++u) {
+                cmacc(E[idx[u][0] * 4 + idx[u][1]], dl[idx[u][0]], p[idx[u][1]]);
+                cmacc(E[idx[u][0] * 4 + idx[u][1]], l[idx[u][0]], dp[idx[u][1]]);
             }
             if (a.update) {
                 double2 q[4];
-                if (MODE == kGeneral) {
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        q[i] = zero2();
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            cmacc(q[i], sg[c * 4 + i], dl[c]);
-                            cmacc(q[i], sx[c * 4 + i], l[c]);
-                        }
-                    }
-                } else {
-                    q[0] = zero2(); cmacc(q[0], sg[0], dl[0]); cmacc(q[0], sg[12], dl[3]);
-                    cmacc(q[0], sx[0], l[0]); cmacc(q[0], sx[12], l[3]);
-                    q[3] = zero2(); cmacc(q[3], sg[3], dl[0]); cmacc(q[3], sg[15], dl[3]);
-                    cmacc(q[3], sx[3], l[0]); cmacc(q[3], sx[15], l[3]);
-                    q[1] = zero2(); cmacc(q[1], sg[5], dl[1]); cmacc(q[1], sg[9], dl[2]);
-                    cmacc(q[1], sx[5], l[1]); cmacc(q[1], sx[9], l[2]);
-                    q[2] = zero2(); cmacc(q[2], sg[6], dl[1]); cmacc(q[2], sg[10], dl[2]);
-                    cmacc(q[2], sx[6], l[1]); cmacc(q[2], sx[10], l[2]);
-                }
+                q[0] = zero2(); cmacc(q[0], sg[0], dl[0]); cmacc(q[0], sg[12], dl[3]);
+                cmacc(q[0], sx[0], l[0]); cmacc(q[0], sx[12], l[3]);
+                q[3] = zero2(); cmacc(q[3], sg[3], dl[0]); cmacc(q[3], sg[15], dl[3]);
+                cmacc(q[3], sx[3], l[0]); cmacc(q[3], sx[15], l[3]);
+                q[1] = zero2(); cmacc(q[1], sg[5], dl[1]); cmacc(q[1], sg[9], dl[2]);
+                cmacc(q[1], sx[5], l[1]); cmacc(q[1], sx[9], l[2]);
+                q[2] = zero2(); cmacc(q[2], sg[6], dl[1]); cmacc(q[2], sg[10], dl[2]);
+                cmacc(q[2], sx[6], l[1]); cmacc(q[2], sx[10], l[2]);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) a.dlam[off[c]] = q[c];
             }
@@ -412,6 +586,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_dir(const BwdArgs a) {
             }
         }
     }
+    if constexpr (MODE == kGeneral) env3_finish(K1, K2, K3, E);
     block_reduce_store(E, a.part + (long long)blockIdx.x * kEnvDoubles);
 }
 

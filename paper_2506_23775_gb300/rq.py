@@ -25,7 +25,7 @@ EXPORTS = ("rq_create", "rq_destroy", "rq_setup_target", "rq_set_columns", "rq_s
            "rq_cost_static", "rq_set_gradient_space", "rq_batch_create", "rq_batch_destroy",
            "rq_batch_add", "rq_batch_set_tile", "rq_batch_hvp", "rq_batch_info", "rq_batch_last_error",
            "rq_set_arithmetic", "rq_set_translation", "rq_hessian", "rq_set_checkpointing",
-           "rq_set_graphs", "rq_set_checks", "rq_last_error")
+           "rq_set_graphs", "rq_set_checks", "rq_set_first_layer", "rq_last_error")
 
 
 class RQCircuit(C.Structure):
@@ -101,6 +101,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "rq_set_checkpointing": ([vp, C.c_int], C.c_int),
         "rq_set_graphs": ([vp, C.c_int], C.c_int),
         "rq_set_checks": ([vp, C.c_int], C.c_int),
+        "rq_set_first_layer": ([vp, C.c_int], C.c_int),
         "rq_batch_create": ([C.POINTER(vp), C.c_int], C.c_int),
         "rq_batch_destroy": ([vp], C.c_int),
         "rq_batch_add": ([vp, C.POINTER(RQTarget), C.POINTER(RQCircuit), C.POINTER(C.c_int)], C.c_int),
@@ -216,6 +217,10 @@ class Context:
         """Keep the forward state every ``interval`` gates (1: every gate) and
         recompute the rest in the backward pass."""
         self._check(self._lib.rq_set_checkpointing(self._h, int(interval)))
+
+    def set_first_layer(self, enable: bool):
+        """Sweep only the nonzero items of the first layer's gates (default on)."""
+        self._check(self._lib.rq_set_first_layer(self._h, 1 if enable else 0))
 
     def set_checks(self, enable: bool):
         """Validate the gates of every call (unitarity, parity pattern)."""
