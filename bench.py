@@ -43,7 +43,8 @@ HBM_FALLBACK_GBS = 6800.0
 # (profiles/bwd_gate_dir_n16_tile512_dram.md).  It holds only for the kernel
 # source it was taken on, so the sources are hashed and compared at run time.
 TRAFFIC = {"kernel": "bwd_gate_dir", "bytes_per_launch": None, "sha256": None,
-           "sources": ("paper_2506_23775_gb300/csrc/rq_sweep.cu", "paper_2506_23775_gb300/csrc/rq_internal.h")}
+           "sources": ("paper_2506_23775_gb300/csrc/rq_sweep.cu", "paper_2506_23775_gb300/csrc/rq_items.cuh",
+                       "paper_2506_23775_gb300/csrc/rq_internal.h")}
 
 
 def _kernel_sources_sha256():

@@ -200,12 +200,12 @@ rq_status rq_set_translation(rq_ctx *ctx, int shift_sites);
  * (paper Eq. f_target_sum_unit_vec), so before gate l of the leading run of
  * pairwise disjoint gates (the first brickwall layer) psi of column j
  * differs from |j> only on the qubits of the earlier gates of the run: the
- * FP64 general-gate sweeps of those gates visit only the 4^(l-1) items per
- * column where psi can be nonzero (forward and backward; the adjoint state is
- * read later only on that set), about 8 % of the work of a 78-gate n = 16
- * circuit.  The results equal the full sweeps up to the order of the sums
- * (~1e-16 relative).  enable = 0 sweeps every item; parity gates and the
- * double-float sweeps always do. */
+ * sweeps of those gates (FP64 and double-float) visit only the 4^(l-1) items
+ * per column where psi can be nonzero (forward and backward; the adjoint
+ * state is read later only on that set), about 8 % of the work of a 78-gate
+ * n = 16 circuit.  The results equal the full sweeps up to the order of the
+ * sums (~1e-16 relative).  A parity gate on the implied qubit 0 sweeps all of
+ * its items.  enable = 0 sweeps every item. */
 rq_status rq_set_first_layer(rq_ctx *ctx, int enable);
 
 /* Gate validation, off by default.  With enable = 1 every rq_cost, rq_grad,

@@ -690,7 +690,7 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
             RQ_LAUNCHED();
         }
     }
-    const bool first_layer = ctx->first_layer && !df;  // the df64 kernels sweep every item
+    const bool first_layer = ctx->first_layer;
     const double2 *gsrc = df ? ctx->d_gates_df : ctx->d_gates;
     const double2 *dsrc = df ? ctx->d_dirs_df : ctx->d_dirs;
     const int B = ctx->B;
@@ -1176,20 +1176,25 @@ rq_status rq_setup_target(rq_ctx *ctx, const rq_target *tgt, const rq_circuit *c
             gg.qfirst = a != 0 ? 1 : 0;
         }
     }
-    // The leading run of pairwise disjoint general gates acts on a basis
-    // state: before gate l of the run only the qubits of the earlier gates of
-    // the run can differ from the column's basis state.
-    if (ctx->structure == 0) {
+    // The leading run of pairwise disjoint gates acts on a basis state: before
+    // gate l of the run only the qubits of the earlier gates of the run can
+    // differ from the column's basis state (bit masks in stored coordinates;
+    // the implied qubit of the parity layout has no stored bit).  Gates on two
+    // stored qubits then sweep only those items; a parity gate on the implied
+    // qubit sweeps all of its (two-amplitude) items.
+    {
         const long long all = ctx->n_store - 1;
         long long used = 0;
         for (int l = 0; l < ctx->g; ++l) {
             GateGeom &gg = ctx->geo[l];
-            const long long bits = (1LL << gg.pa) | (1LL << gg.pb);
+            const long long bits = gg.mode == rq::kParity2 ? (1LL << gg.pa) : (1LL << gg.pa) | (1LL << gg.pb);
             if (used & bits) break;
-            gg.free_bits = used;
+            if (gg.mode != rq::kParity2) {
+                gg.free_bits = used;
+                gg.fixed_bits = all & ~(used | bits);
+                gg.restricted = gg.fixed_bits != 0;
+            }
             used |= bits;
-            gg.fixed_bits = all & ~used;
-            gg.restricted = gg.fixed_bits != 0;
         }
     }
     rq_status st = tgt->model == 2 ? build_target_dense(ctx, tgt->dense_U) : build_target(ctx);

@@ -49,15 +49,11 @@
 // the FP64 instructions of a general-gate item by 12.5-17 %; the parity-gate
 // paths touch two entries per row, where the per-amplitude sums cost as much
 // as they save, so they keep the four-product form.
-#include "rq_internal.h"
+#include "rq_items.cuh"
 
 namespace rq {
 namespace {
 
-__device__ __forceinline__ long long insert_zero(long long r, int p) {
-    const long long lo = r & ((1LL << p) - 1);
-    return ((r >> p) << (p + 1)) | lo;
-}
 
 // acc += a * b
 __device__ __forceinline__ void cmac(double2 &acc, const double2 a, const double2 b) {
@@ -177,50 +173,6 @@ __device__ __forceinline__ void env3_finish(const double (&K1)[16], const double
     for (int i = 0; i < 16; ++i) E[i] = make_double2(K1[i] + K3[i], K1[i] + K2[i]);
 }
 
-// Stored offsets of the four amplitudes of an item whose amplitude with both
-// gate bits clear is x0, for a gate on stored bits pa (first listed) and pb.
-__device__ __forceinline__ void offsets4_at(long long x0, long long b, int pa, int pb, int log2B,
-                                            long long (&off)[4]) {
-    const long long sa = 1LL << pa, sb = 1LL << pb;
-    off[0] = (x0 << log2B) | b;
-    off[1] = ((x0 | sb) << log2B) | b;
-    off[2] = ((x0 | sa) << log2B) | b;
-    off[3] = ((x0 | sa | sb) << log2B) | b;
-}
-
-// ... of item (r, b): r enumerates the other n - 2 stored bits.
-__device__ __forceinline__ void offsets4(long long r, long long b, int pa, int pb, int log2B,
-                                         long long (&off)[4]) {
-    const int plo = pa < pb ? pa : pb;
-    const int phi = pa < pb ? pb : pa;
-    offsets4_at(insert_zero(insert_zero(r, plo), phi), b, pa, pb, log2B, off);
-}
-
-// The low bits of t placed, in order, at the set bits of mask.
-__device__ __forceinline__ long long deposit_bits(long long t, long long mask) {
-    long long out = 0;
-    for (long long m = mask; m != 0; m &= m - 1, t >>= 1)
-        if (t & 1) out |= m & -m;
-    return out;
-}
-
-// Offsets of item (t, b) of a general gate.  Unrestricted: t = r.  A gate of
-// the leading run of disjoint gates (geo.restricted, with the tile's columns):
-// t enumerates only the free bits, the fixed bits are those of column b's
-// basis state, where psi_{l-1} can be nonzero.  Returns false for a padding
-// column (nothing to do).
-__device__ __forceinline__ bool general_item(const GateGeom &geo, const int32_t *cols, long long t, long long b,
-                                             int log2B, long long (&off)[4]) {
-    if (cols != nullptr && geo.restricted) {
-        const int j = cols[b];
-        if (j < 0) return false;
-        offsets4_at(deposit_bits(t, geo.free_bits) | ((long long)j & geo.fixed_bits), b, geo.pa, geo.pb, log2B, off);
-        return true;
-    }
-    offsets4(t, b, geo.pa, geo.pb, log2B, off);
-    return true;
-}
-
 // kParity2 item: the two stored amplitudes differ in the stored qubit at
 // bit p; e = bit of the implied qubit for the first one.  Returns the local
 // 4x4 indices (i0, i1) of the two amplitudes.
@@ -266,7 +218,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fwd(const FwdArgs a) {
         const long long b = it & Bm, r = it >> a.log2B;
         if constexpr (MODE == kGeneral) {
             long long off[4];
-            if (!general_item(a.geo, a.cols, r, b, a.log2B, off)) continue;
+            if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
             Amp3 x[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) x[c] = amp3(__ldg(&a.psi_in[off[c]]));
@@ -286,7 +238,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fwd(const FwdArgs a) {
             }
         } else if constexpr (MODE == kParity4) {
             long long off[4];
-            offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
+            if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
             double2 p[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) p[c] = __ldg(&a.psi_in[off[c]]);
@@ -398,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_base(const BwdArgs a) {
         const long long b = it & Bm, r = it >> a.log2B;
         if constexpr (MODE == kGeneral) {
             long long off[4];
-            if (!general_item(a.geo, a.cols, r, b, a.log2B, off)) continue;
+            if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
             Amp3 l[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) l[c] = amp3(a.lam[off[c]]);
@@ -416,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_base(const BwdArgs a) {
             }
         } else if constexpr (MODE == kParity4) {
             long long off[4];
-            offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
+            if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
             double2 l[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) l[c] = a.lam[off[c]];
@@ -505,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_dir(const BwdArgs a) {
         const long long b = it & Bm, r = it >> a.log2B;
         if constexpr (MODE == kGeneral) {
             long long off[4];
-            if (!general_item(a.geo, a.cols, r, b, a.log2B, off)) continue;
+            if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
             Amp3 l[4], dl[4], p[4], dp[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -524,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_dir(const BwdArgs a) {
             }
         } else if constexpr (MODE == kParity4) {
             long long off[4];
-            offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
+            if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
             double2 l[4], dl[4], p[4], dp[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {

@@ -23,7 +23,7 @@
 // target overlap, the reductions and the Riemannian post-processing stay FP64.
 // Every float operation below is an explicitly rounded intrinsic, so the
 // compiler can neither contract nor reassociate the error-free transforms.
-#include "rq_internal.h"
+#include "rq_items.cuh"
 
 namespace rq {
 namespace {
@@ -107,21 +107,7 @@ __device__ __forceinline__ double2 to_double(const CAcc &c) {
     return make_double2((double)c.re.h + (double)c.re.l, (double)c.im.h + (double)c.im.l);
 }
 
-__device__ __forceinline__ long long insert_zero(long long r, int p) {
-    const long long lo = r & ((1LL << p) - 1);
-    return ((r >> p) << (p + 1)) | lo;
-}
 
-__device__ __forceinline__ void offsets4(long long r, long long b, int pa, int pb, int log2B, long long (&off)[4]) {
-    const int plo = pa < pb ? pa : pb;
-    const int phi = pa < pb ? pb : pa;
-    const long long x0 = insert_zero(insert_zero(r, plo), phi);
-    const long long sa = 1LL << pa, sb = 1LL << pb;
-    off[0] = (x0 << log2B) | b;
-    off[1] = ((x0 | sb) << log2B) | b;
-    off[2] = ((x0 | sa) << log2B) | b;
-    off[3] = ((x0 | sa | sb) << log2B) | b;
-}
 
 __device__ __forceinline__ void offsets2(long long r, long long b, int p, int qfirst, int parity, int log2B,
                                          long long (&off)[2], int &i0, int &i1) {
@@ -196,7 +182,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fwd_df(const FwdArgs a) {
         const long long b = it & Bm, r = it >> a.log2B;
         if (MODE == kGeneral || MODE == kParity4) {
             long long off[4];
-            offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
+            if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
             float4 p[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) p[c] = __ldg(&psi_in[off[c]]);
@@ -288,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_base_df(const BwdArgs a) {
         const long long b = it & Bm, r = it >> a.log2B;
         if (MODE == kGeneral || MODE == kParity4) {
             long long off[4];
-            offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
+            if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
             float4 l[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) l[c] = lam[off[c]];
@@ -378,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_dir_df(const BwdArgs a) {
         const long long b = it & Bm, r = it >> a.log2B;
         if (MODE == kGeneral || MODE == kParity4) {
             long long off[4];
-            offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
+            if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
             float4 l[4], dl[4], p[4], dp[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -525,7 +511,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_dir_df2(const BwdArgs a) {
     for (long long it = start; it < a.n_items; it += stride) {
         const long long b = it & Bm, r = it >> a.log2B;
         long long off[4];
-        offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
+        if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
         float4 l[4], dl[4], p[4], dp[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -616,7 +602,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_base_df2(const BwdArgs a) {
     for (long long it = start; it < a.n_items; it += stride) {
         const long long b = it & Bm, r = it >> a.log2B;
         long long off[4];
-        offsets4(r, b, a.geo.pa, a.geo.pb, a.log2B, off);
+        if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
         float4 l[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) l[c] = lam[off[c]];

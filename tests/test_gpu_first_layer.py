@@ -28,13 +28,17 @@ def _both(rq, prob, setup, gates, X):
     return out
 
 
-@pytest.mark.parametrize("case", ["full", "padded_range", "checkpointed", "four_dirs", "small_tile"])
-def test_first_layer_matches_full_sweeps(rq, case):
-    prob = w.config_problem("small" if case != "checkpointed" else "tied12", structure=0)
+@pytest.mark.parametrize("case,structure,arith", [
+    ("full", 0, 0), ("padded_range", 0, 0), ("checkpointed", 0, 0), ("four_dirs", 0, 0), ("small_tile", 0, 0),
+    ("full", 1, 0), ("checkpointed", 1, 0), ("four_dirs", 1, 0),
+    ("full", 0, 1), ("padded_range", 0, 1), ("full", 1, 1), ("four_dirs", 1, 1)])
+def test_first_layer_matches_full_sweeps(rq, case, structure, arith):
+    prob = w.config_problem("small" if case != "checkpointed" else "tied12", structure=structure)
     k = 4 if case == "four_dirs" else 1
     X = w.random_directions(prob.n_params, k, 31)
 
     def setup(ctx):
+        ctx.set_arithmetic(arith)
         if case == "padded_range":
             ctx.set_columns(3, 200)   # not a multiple of the tile: padding columns
         if case == "checkpointed":
@@ -44,6 +48,12 @@ def test_first_layer_matches_full_sweeps(rq, case):
             ctx.set_tile(16, 2)
 
     off, on = _both(rq, prob, setup, prob.gates, X)
+    if arith == 1:  # double-float: the same sums in another order, ~48-bit arithmetic
+        assert abs(on[0] - off[0]) <= 1e-12 * abs(off[0])
+        assert_close(on[1], off[1], prob.n, rtol=1e-12, what="rgrad")
+        for i in range(k):
+            assert_close(on[2][i], off[2][i], prob.n, rtol=1e-12, what=f"hvp {i}")
+        return
     assert abs(on[0] - off[0]) <= 1e-13 * abs(off[0])
     assert_close(on[1], off[1], prob.n, rtol=1e-13, what="rgrad")
     for i in range(k):
