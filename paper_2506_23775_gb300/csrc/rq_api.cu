@@ -1083,6 +1083,8 @@ rq_status rq_create(rq_ctx **out, int device, void *cuda_stream) {
                     cudaGetErrorString(e));
     if ((e = cudaSetDevice(device)) != cudaSuccess)
         return fail(nullptr, RQ_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    if ((e = rq::init_sweep_attributes()) != cudaSuccess)
+        return fail(nullptr, RQ_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
     rq_ctx *ctx = new rq_ctx();
     ctx->device = device;
     cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);

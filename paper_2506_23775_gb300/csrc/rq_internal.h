@@ -86,6 +86,8 @@ struct TargetDev {
 };
 
 // Launchers (rq_sweep.cu).
+// Once per device before the first sweep launch (shared-memory limits).
+cudaError_t init_sweep_attributes();
 void launch_fwd(const FwdArgs &a, int grid, cudaStream_t s);
 void launch_bwd_base(const BwdArgs &a, int grid, cudaStream_t s);
 void launch_bwd_dir(const BwdArgs &a, int grid, cudaStream_t s);

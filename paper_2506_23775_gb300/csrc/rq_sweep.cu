@@ -74,8 +74,9 @@ __device__ __forceinline__ void cmacc(double2 &acc, const double2 a, const doubl
 __device__ __forceinline__ double2 zero2() { return make_double2(0.0, 0.0); }
 
 // A general 4x4 complex matrix tabulated for the three-product form:
-// s = a + b, a, nb = -b of each entry m = a + ib, row-major.
-struct Mat3 {
+// s = a + b, a, nb = -b of each entry m = a + ib, row-major (16-byte aligned,
+// so two neighbouring entries of a row load as one 128-bit shared load).
+struct __align__(16) Mat3 {
     double s[16], a[16], nb[16];
 };
 
@@ -171,6 +172,64 @@ __device__ __forceinline__ void env3_finish(const double (&K1)[16], const double
                                             double2 (&E)[16]) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) E[i] = make_double2(K1[i] + K3[i], K1[i] + K2[i]);
+}
+
+// ------------------------------------------------ pipelined item loads --
+//
+// The general-gate backward kernels hold ~210 registers, so an SM runs only
+// eight of their warps; while a warp waits for its item's amplitudes from
+// HBM, the FP64 pipe depends on the others.  Their grid-stride loops
+// therefore copy the next item's amplitudes into this thread's own slots of
+// shared memory (cp.async, two stages) while the current item is computed.
+// Slot (stage, c) of thread t is at [(stage * NA + c) * kThreads + t], so a
+// warp's copies and reads of one slot are contiguous.
+
+__device__ __forceinline__ void cp_async16(double2 *smem, const double2 *gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int kDirSlots = 16;   // k_bwd_dir: lambda, lambda', psi, psi' (4 amplitudes each)
+constexpr int kBaseSlots = 8;   // k_bwd_base: lambda, psi
+constexpr size_t kDirSmem = sizeof(double2) * 2 * kDirSlots * kThreads;
+constexpr size_t kBaseSmem = sizeof(double2) * 2 * kBaseSlots * kThreads;
+
+// Grid-stride loop over items with the loads of item i + stride in flight
+// while item i is computed.  offsets(it, off) -> false for an item with
+// nothing to do; issue(off, stage) starts its copies; body(off, stage)
+// computes it from the slots.
+template <class Offsets, class Issue, class Body>
+__device__ __forceinline__ void pipelined_items(long long n_items, Offsets offsets, Issue issue, Body body) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long off[4], nxt[4];
+    bool ok = false;
+    if (it < n_items) {
+        ok = offsets(it, off);
+        if (ok) issue(off, 0);
+    }
+    cp_async_commit();
+    int st = 0;
+    for (; it < n_items; it += stride) {
+        bool ok_next = false;
+        if (it + stride < n_items) {
+            ok_next = offsets(it + stride, nxt);
+            if (ok_next) issue(nxt, st ^ 1);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();  // this item's copies have landed
+        if (ok) body(off, st);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) off[c] = nxt[c];
+        ok = ok_next;
+        st ^= 1;
+    }
+    cp_async_wait<0>();
 }
 
 // kParity2 item: the two stored amplitudes differ in the stored qubit at
@@ -345,28 +404,45 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_base(const BwdArgs a) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) K1[i] = K2[i] = K3[i] = 0.0;
     const long long Bm = (1LL << a.log2B) - 1;
+    if constexpr (MODE == kGeneral) {
+        extern __shared__ double2 pf[];
+        double2 *mine = pf + threadIdx.x;
+        auto slot = [&](int st, int c) { return mine + (st * kBaseSlots + c) * kThreads; };
+        pipelined_items(
+            a.n_items,
+            [&](long long it, long long (&off)[4]) {
+                return item_offsets4(a.geo, a.cols, it >> a.log2B, it & Bm, a.log2B, off);
+            },
+            [&](const long long (&off)[4], int st) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    cp_async16(slot(st, c), a.lam + off[c]);
+                    if (accumulate) cp_async16(slot(st, 4 + c), a.psi + off[c]);
+                }
+            },
+            [&](const long long (&off)[4], int st) {
+                Amp3 l[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) l[c] = amp3(*slot(st, c));
+                if (accumulate) {
+                    Amp3 p[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) p[c] = amp3(*slot(st, 4 + c));
+                    env3(K1, K2, K3, l, p);
+                }
+                if (a.update) {
+                    double2 q[4];
+                    matvec3(sgT3, l, q);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) a.lam[off[c]] = q[c];
+                }
+            });
+    }
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.n_items; it += stride) {
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; MODE != kGeneral && it < a.n_items;
+         it += stride) {
         const long long b = it & Bm, r = it >> a.log2B;
-        if constexpr (MODE == kGeneral) {
-            long long off[4];
-            if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
-            Amp3 l[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) l[c] = amp3(a.lam[off[c]]);
-            if (accumulate) {
-                Amp3 p[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) p[c] = amp3(__ldg(&a.psi[off[c]]));
-                env3(K1, K2, K3, l, p);
-            }
-            if (a.update) {
-                double2 q[4];
-                matvec3(sgT3, l, q);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) a.lam[off[c]] = q[c];
-            }
-        } else if constexpr (MODE == kParity4) {
+        if constexpr (MODE == kParity4) {
             long long off[4];
             if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
             double2 l[4];
@@ -452,29 +528,48 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_dir(const BwdArgs a) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) K1[i] = K2[i] = K3[i] = 0.0;
     const long long Bm = (1LL << a.log2B) - 1;
+    if constexpr (MODE == kGeneral) {
+        extern __shared__ double2 pf[];
+        double2 *mine = pf + threadIdx.x;
+        auto slot = [&](int st, int c) { return mine + (st * kDirSlots + c) * kThreads; };
+        pipelined_items(
+            a.n_items,
+            [&](long long it, long long (&off)[4]) {
+                return item_offsets4(a.geo, a.cols, it >> a.log2B, it & Bm, a.log2B, off);
+            },
+            [&](const long long (&off)[4], int st) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    cp_async16(slot(st, c), a.lam + off[c]);
+                    cp_async16(slot(st, 4 + c), a.dlam + off[c]);
+                    cp_async16(slot(st, 8 + c), a.psi + off[c]);
+                    cp_async16(slot(st, 12 + c), a.dpsi + off[c]);
+                }
+            },
+            [&](const long long (&off)[4], int st) {
+                Amp3 l[4], dl[4], p[4], dp[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    l[c] = amp3(*slot(st, c));
+                    dl[c] = amp3(*slot(st, 4 + c));
+                    p[c] = amp3(*slot(st, 8 + c));
+                    dp[c] = amp3(*slot(st, 12 + c));
+                }
+                env3(K1, K2, K3, dl, p);
+                env3(K1, K2, K3, l, dp);
+                if (a.update) {
+                    double2 q[4];
+                    matvec3_pair(sgT3, dl, sxT3, l, q);  // G^dagger lambda' + X^dagger lambda
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) a.dlam[off[c]] = q[c];
+                }
+            });
+    }
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.n_items; it += stride) {
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; MODE != kGeneral && it < a.n_items;
+         it += stride) {
         const long long b = it & Bm, r = it >> a.log2B;
-        if constexpr (MODE == kGeneral) {
-            long long off[4];
-            if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
-            Amp3 l[4], dl[4], p[4], dp[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                l[c] = amp3(__ldg(&a.lam[off[c]]));
-                dl[c] = amp3(a.dlam[off[c]]);
-                p[c] = amp3(__ldg(&a.psi[off[c]]));
-                dp[c] = amp3(__ldg(&a.dpsi[off[c]]));
-            }
-            env3(K1, K2, K3, dl, p);
-            env3(K1, K2, K3, l, dp);
-            if (a.update) {
-                double2 q[4];
-                matvec3_pair(sgT3, dl, sxT3, l, q);  // G^dagger lambda' + X^dagger lambda
-#pragma unroll
-                for (int c = 0; c < 4; ++c) a.dlam[off[c]] = q[c];
-            }
-        } else if constexpr (MODE == kParity4) {
+        if constexpr (MODE == kParity4) {
             long long off[4];
             if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
             double2 l[4], dl[4], p[4], dp[4];
@@ -564,7 +659,7 @@ void launch_fwd(const FwdArgs &a, int grid, cudaStream_t s) {
 
 void launch_bwd_base(const BwdArgs &a, int grid, cudaStream_t s) {
     switch (a.geo.mode) {
-        case kGeneral: k_bwd_base<kGeneral><<<grid, kThreads, 0, s>>>(a); break;
+        case kGeneral: k_bwd_base<kGeneral><<<grid, kThreads, kBaseSmem, s>>>(a); break;
         case kParity4: k_bwd_base<kParity4><<<grid, kThreads, 0, s>>>(a); break;
         default: k_bwd_base<kParity2><<<grid, kThreads, 0, s>>>(a); break;
     }
@@ -572,10 +667,20 @@ void launch_bwd_base(const BwdArgs &a, int grid, cudaStream_t s) {
 
 void launch_bwd_dir(const BwdArgs &a, int grid, cudaStream_t s) {
     switch (a.geo.mode) {
-        case kGeneral: k_bwd_dir<kGeneral><<<grid, kThreads, 0, s>>>(a); break;
+        case kGeneral: k_bwd_dir<kGeneral><<<grid, kThreads, kDirSmem, s>>>(a); break;
         case kParity4: k_bwd_dir<kParity4><<<grid, kThreads, 0, s>>>(a); break;
         default: k_bwd_dir<kParity2><<<grid, kThreads, 0, s>>>(a); break;
     }
+}
+
+cudaError_t init_sweep_attributes() {
+    // the pipelined general-gate kernels keep two stages of item slots in
+    // dynamic shared memory (128 KB and 64 KB per CTA)
+    cudaError_t e = cudaFuncSetAttribute(k_bwd_dir<kGeneral>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kDirSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_bwd_base<kGeneral>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBaseSmem);
+    return e;
 }
 
 void launch_init_unit(double2 *psi0, const int32_t *cols, int B, int log2B, long long n_store,
