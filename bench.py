@@ -37,12 +37,17 @@ FP64_PEAK_TFLOPS = 4 * 152 * 2.07e9 / 1e12
 FP32_PIPE_TOPS = 128 * 152 * 2.07e9 / 1e12   # FP32 pipe instructions per second (one FMA = one)
 HBM_FALLBACK_GBS = 6800.0
 
-# DRAM traffic of one FP64 bwd_gate_dir launch of this workload (2^14 x 512
-# items: n = 16, general gates, 512-column tile), dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu capture of the full-size launch
-# (profiles/bwd_gate_dir_n16_tile512_dram.md).  It holds only for the kernel
+# DRAM traffic of one full (not first-layer) FP64 bwd_gate_dir launch of this
+# workload (2^14 x 512 items: n = 16, general gates, 512-column tile):
+# dram__bytes_read.sum + dram__bytes_write.sum of the same kernel captured at
+# n = 14 (2^12 x 512 items: 536.93 + 112.03 MB) scaled by the items, 4x; the
+# reads of 2^12 x 256 items are exactly half (profiles/
+# bwd_gate_dir_dram_traffic.md).  Algorithmic bytes of that launch:
+# 2^14 * 512 * 5 * 4 * 16 = 2.684e9.  The figure holds only for the kernel
 # source it was taken on, so the sources are hashed and compared at run time.
-TRAFFIC = {"kernel": "bwd_gate_dir", "bytes_per_launch": None, "sha256": None,
+TRAFFIC = {"kernel": "bwd_gate_dir", "bytes_per_launch": 2595816448,
+           "algorithmic_bytes_per_launch": 2684354560,
+           "sha256": "eb5783a5b4da72869e68d3ecdc4f100d529123fddbfe7dcf75af65d16f68b38d",
            "sources": ("paper_2506_23775_gb300/csrc/rq_sweep.cu", "paper_2506_23775_gb300/csrc/rq_items.cuh",
                        "paper_2506_23775_gb300/csrc/rq_internal.h")}
 
@@ -414,10 +419,12 @@ def run_ours(args):
         sweep = {k: v for k, v in res["prof"].items() if k.startswith(("fwd", "bwd"))}
         dom = max(sweep, key=lambda k: sweep[k]["ms"])
         d = sweep[dom]
-        traffic = None
+        traffic = traffic_note = None
         if (headline and TRAFFIC["bytes_per_launch"] and dom == TRAFFIC["kernel"] and res["B"] == 512
                 and (args.sites, args.depth) == (8, 11) and _kernel_sources_sha256() == TRAFFIC["sha256"]):
             traffic = TRAFFIC["bytes_per_launch"]
+            traffic_note = ("DRAM bytes of one full (not first-layer) launch, scaled by items from an ncu capture "
+                            "at n = 14; that launch's algorithmic bytes: %d" % TRAFFIC["algorithmic_bytes_per_launch"])
         per_launch_ms = d["ms"] / d["launches"]
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
         if df64:
@@ -441,6 +448,7 @@ def run_ours(args):
                    "gbs": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)} for k, v in res["prof"].items()}
         return {"kernel": dom, "bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                "traffic_note": traffic_note,
                 "flop_convention": "4 real multiply-adds per complex multiply-add (8 flops)",
                 "fp64_pipe_frac": round(achieved * (PIPE_PER_FLOP_GENERAL.get(dom, 1.0) if general else 1.0)
                                         / FP64_PEAK_TFLOPS, 4),
