@@ -371,6 +371,54 @@ def run_ours(args):
                                 "cost/grad/hvp, full basis sums; contexts warmed on 6 requests first"})
         return out
 
+    def measure_rates(steps: int = 3):
+        """f only, f + grad, and f + grad + 4 HVPs at the benchmark instance
+        (general gates, FP64, 512-column tiles): evals/s of each kind, timed
+        with CUDA events over `steps` tiles after one warm-up tile."""
+        prob = make_workload(args, 0)
+        X4 = w.random_directions(prob.n_params, 4, 1602)
+        ctx = rq.Context(local, stream=stream.cuda_stream).setup_problem(prob)
+        ncols = 1 << prob.n
+        ctx.set_columns(0, 512)
+        B = ctx.info()["columns_per_tile"]
+        gates = torch.from_numpy(prob.gates.copy()).to(dev)
+        dirs = torch.from_numpy(X4.copy()).to(dev)
+        f_t = torch.zeros(1, dtype=torch.float64, device=dev)
+        rg_t = torch.zeros_like(gates)
+        hv_t = torch.zeros_like(dirs)
+        kinds = {
+            "cost": lambda: ctx.cost_dev(gates.data_ptr(), f_t.data_ptr()),
+            "grad": lambda: ctx.grad_dev(gates.data_ptr(), f_t.data_ptr(), rg_t.data_ptr()),
+            "hvp_k4": lambda: ctx.hvp_dev(gates.data_ptr(), dirs.data_ptr(), 4, f_t.data_ptr(), rg_t.data_ptr(),
+                                          hv_t.data_ptr()),
+        }
+        out = {}
+        for name, call in kinds.items():
+            if name == "hvp_k4":
+                # all four directions in one sweep (kc = 4): 128-column tiles keep
+                # the (1 + 4)(g + 1) checkpointed states within the HBM budget
+                ctx.set_tile(128, 4)
+            B = ctx.info()["columns_per_tile"]
+            ctx.set_columns(0, B)
+            call()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for s_ in range(steps):
+                c0 = ((s_ + 1) * B) % ncols
+                ctx.set_columns(c0, c0 + B)
+                call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            out[name] = {"evals_per_s": steps * B / ncols / (ms * 1e-3), "ms_per_tile": ms / steps,
+                         "columns_per_tile": B, "directions_per_sweep": ctx.info()["max_dirs"]}
+        out["hvp_k4"]["hvps_per_s"] = 4 * out["hvp_k4"]["evals_per_s"]
+        out["note"] = ("one eval = the whole basis sum; cost = f; grad = f + Riemannian gradient; hvp_k4 = f + "
+                       "gradient + 4 Riemannian HVPs sharing the forward and adjoint states")
+        ctx.close()
+        return out
+
     def measure_sweeps():
         """Gradient time per basis summand (the paper's Fig. matchgate_gradient):
         spinful chains with 5 layers for n = 6..16, and n = 10 for 1..21 layers;
@@ -407,6 +455,7 @@ def run_ours(args):
     batched = measure_batched() if (not args.no_batched and world == 1) else None
     served = measure_served() if (not args.no_served and world == 1) else None
     sweeps = measure_sweeps() if (args.sweeps and world == 1) else None
+    kind_rates = measure_rates() if (not args.general_only and world == 1) else None
 
     if rank != 0:
         if world > 1:
@@ -489,6 +538,8 @@ def run_ours(args):
         line["served"] = served
     if sweeps is not None:
         line["sweeps"] = sweeps
+    if kind_rates is not None:
+        line["rates"] = kind_rates
     if world == 1 and not args.no_cpu:
         rates, cores, ncols = cpu_oracle_rate(per_worker=1, repeats=2)   # first round warms up
         line["cpu_baseline"] = {"value": rates[-1], "unit": UNIT, "cores": cores, "kind": "oracle",
