@@ -358,9 +358,10 @@ def run_ours(args):
         out["plain_poisson_80pct"] = srv.run(serve.poisson_stream(probs, kinds, rate_hz=0.8 * capacity, seed=503),
                                              realtime=True)
         srv.close()
-        for name, rate in (("served_burst", 1e9), ("served_poisson_80pct", 0.8 * capacity)):
+        for name, rate, aging in (("served_burst", 1e9, 0.0), ("served_poisson_80pct", 0.8 * capacity, 0.0),
+                                  ("served_poisson_80pct_aging", 0.8 * capacity, 1.0)):
             srv = serve.Server(local, max_inflight=8, tile=128, contexts_per_problem=2, setup_workers=2,
-                               policy="sjf")
+                               policy="sjf", aging=aging)
             srv.run(serve.poisson_stream(probs[:6], kinds[:6], rate_hz=1e9, seed=7), realtime=False)
             out[name] = srv.run(serve.poisson_stream(probs, kinds, rate_hz=rate, seed=503),
                                 realtime=rate < 1e8)

@@ -58,6 +58,12 @@ def work_flops(req: "Request") -> float:
     return units * p.n_gates * 32.0 * 4.0 ** p.n / (4.0 if p.structure == 1 else 1.0)
 
 
+def admission_key(req: "Request", now: float, aging: float, fp64_flops_per_s: float) -> float:
+    """Shortest-work-first order with aging: estimated seconds of work minus
+    ``aging`` times the seconds the request has waited (smaller = sooner)."""
+    return work_flops(req) / fp64_flops_per_s - aging * (now - req.arrival)
+
+
 def gpu_width(p, tile: int, sms: int = 152) -> float:
     """Fraction of the GPU one sweep kernel of this problem fills (its items
     over two 256-thread CTAs per SM)."""
@@ -89,12 +95,16 @@ class Server:
     ``contexts_per_problem``: contexts one problem may hold at once (several
     requests for the same problem then run concurrently); ``setup_workers``:
     host threads that build new contexts (target blocks) while the loop keeps
-    admitting and collecting work.
+    admitting and collecting work.  ``policy``: "fifo" (arrival order) or
+    "sjf" (shortest estimated work first); ``aging``: with "sjf", seconds of
+    estimated work forgiven per second a request has waited, so a large
+    request cannot wait forever behind a stream of small ones (0: pure
+    shortest-first).
     """
 
     def __init__(self, device: int = 0, memory_budget: Optional[int] = None, max_inflight: int = 8,
                  tile: int = 128, contexts_per_problem: int = 2, setup_workers: int = 2,
-                 policy: str = "sjf"):
+                 policy: str = "sjf", aging: float = 0.0, fp64_flops_per_s: float = 1.2e12):
         import concurrent.futures as cf
 
         import torch
@@ -115,6 +125,8 @@ class Server:
         self.stats = collections.Counter()
         self.pool = cf.ThreadPoolExecutor(max_workers=setup_workers)
         self.policy = policy
+        self.aging = aging
+        self.rate = fp64_flops_per_s   # converts work_flops into estimated seconds
         self.sms = torch.cuda.get_device_properties(self.dev).multi_processor_count
 
     # -- contexts ----------------------------------------------------------
@@ -211,7 +223,7 @@ class Server:
             # pipe gains nothing from overlap, and sharing it delays everyone).
             # A request whose problem has no free context does not block others.
             if self.policy == "sjf":
-                waiting.sort(key=work_flops)
+                waiting.sort(key=lambda r: admission_key(r, t, self.aging, self.rate))
             width = sum(gpu_width(r.problem, s.tile, self.sms) for r, s, _, _ in inflight)
             still = []
             for req in waiting:
