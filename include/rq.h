@@ -54,7 +54,7 @@ typedef int rq_status;
 #define RQ_EINVAL (-1)   /* invalid argument (sizes, pairs, indices, NULL) */
 #define RQ_ENOMEM (-2)   /* device workspace does not fit */
 #define RQ_ECUDA (-3)    /* a CUDA runtime call failed */
-#define RQ_ETIMEOUT (-4) /* a bounded device wait expired */
+#define RQ_ETIMEOUT (-4) /* reserved for a bounded device wait; no kernel of this library spins */
 #define RQ_ESTATE (-5)   /* call out of order (no target set up yet) */
 
 /* Circuit topology (paper Sec. "Quantum circuits"): gate l acts on qubits
