@@ -256,12 +256,16 @@ def run_ours(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
             ctx.profile_start()
+            marks = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
             e0.record(stream)
-            for s in range(warmup, warmup + steps):
+            marks[0].record(stream)
+            for i, s in enumerate(range(warmup, warmup + steps)):
                 step(s)
+                marks[i + 1].record(stream)
             e1.record(stream)
             torch.cuda.synchronize()
             prof = ctx.profile_stop()
+            step_ms = [marks[i].elapsed_time(marks[i + 1]) for i in range(steps)]
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -293,7 +297,8 @@ def run_ours(args):
                "d2h_bytes_per_step": int(8 + rg_h.nbytes + hv_h.nbytes)}
         info = ctx.info()
         ctx.close()
-        return dict(value=value, ms_per_step=ms_max / steps, launches=launches, prof=prof, clocks=clk.summary(),
+        return dict(value=value, ms_per_step=ms_max / steps, ms_per_step_median=statistics.median(step_ms),
+                    launches=launches, prof=prof, clocks=clk.summary(),
                     e2e=e2e, batch=batch, B=B, info=info)
 
     def measure_batched():
@@ -443,6 +448,12 @@ def run_ours(args):
         return {"vs_qubits_5_layers": [point(L, 5) for L in (3, 4, 5, 6, 7, 8)],
                 "vs_layers_10_qubits": [point(5, d) for d in (1, 3, 5, 7, 9, 11, 15, 21)]}
 
+    if args.parity_only:   # profiling cases only: the parity-gate sweep alone
+        par = measure(1, args.steps, args.warmup, args.tile)
+        if rank == 0:
+            print(json.dumps({"mode": "parity only (profiling)", "value": par["value"], "unit": UNIT,
+                              "ms_per_step": par["ms_per_step"], "gpu_launches": par["launches"]}))
+        return
     gen = measure(0, args.steps, args.warmup, args.tile)
     par = None
     if not args.general_only:
@@ -511,7 +522,8 @@ def run_ours(args):
 
     line = {
         "metric": METRIC, "value": gen["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": gen["ms_per_step"], "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": gen["ms_per_step"], "ms_per_step_median": gen["ms_per_step_median"],
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "structure": "general", "columns_per_step": gen["batch"],
                    "columns_per_tile": gen["B"], "hvp_directions": 1,
@@ -585,6 +597,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--tile", type=int, default=0, help="columns per tile (power of two; 0 = automatic)")
     ap.add_argument("--general-only", action="store_true", help="skip the parity-gate measurement")
+    ap.add_argument("--parity-only", action="store_true",
+                    help="time only the parity-gate sweep and print a short line (profiling cases only)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-problem batched-vs-plain measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the continuous-batching request stream")
     ap.add_argument("--sweeps", action="store_true", help="also time the gradient per summand vs n and layers")

@@ -27,6 +27,11 @@
 
 using rq::GateGeom;
 
+namespace rq {
+// rq_sweep_df64.cu: shared-memory limits of the double-float kernels
+cudaError_t init_sweep_attributes_df64();
+}  // namespace rq
+
 struct rq_ctx {
     int device = 0;
     int sms = 0;
@@ -1083,7 +1088,7 @@ rq_status rq_create(rq_ctx **out, int device, void *cuda_stream) {
                     cudaGetErrorString(e));
     if ((e = cudaSetDevice(device)) != cudaSuccess)
         return fail(nullptr, RQ_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
-    if ((e = rq::init_sweep_attributes()) != cudaSuccess)
+    if ((e = rq::init_sweep_attributes()) != cudaSuccess || (e = rq::init_sweep_attributes_df64()) != cudaSuccess)
         return fail(nullptr, RQ_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
     rq_ctx *ctx = new rq_ctx();
     ctx->device = device;

@@ -506,8 +506,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_base(const BwdArgs a) {
 // E'[a][c] += conj(lambda'[a]) psi[c] + conj(lambda[a]) psi'[c];
 // lambda' <- G^dagger lambda' + X^dagger lambda.  Runs before the base step
 // of the same gate (it reads lambda_l before that step overwrites it).
+// Parity gates: two CTAs per SM (at most 128 registers; their items carry
+// half the FP64 work of a general item, so more warps are needed to cover
+// the loads).  General gates: one CTA (the three-product sums need ~200).
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 1) k_bwd_dir(const BwdArgs a) {
+__global__ void __launch_bounds__(kThreads, MODE == kGeneral ? 1 : 2) k_bwd_dir(const BwdArgs a) {
     __shared__ double2 sg[16];
     __shared__ double2 sx[16];
     __shared__ Mat3 sgT3, sxT3;  // G^dagger, X^dagger, general gates

@@ -486,10 +486,30 @@ __device__ __forceinline__ void block_reduce_store_half(const CAcc (&acc)[8], do
 // static; the lane's rows are picked with selects (no divergence, no local
 // memory).  For a parity gate row i couples the columns of its block:
 // {0, 3} if i is 0 or 3, else {1, 2}; "even" below is that test.
+// 16-byte asynchronous copy global -> shared (the copying thread sees the data
+// after cp.async.wait_group; its partner lane after a __syncwarp)
+__device__ __forceinline__ void cp_async16_f4(float4 *smem, const float4 *gmem) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_df() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_df() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// k_bwd_dir_df2 keeps two stages of its items' 16 amplitudes per lane pair in
+// dynamic shared memory: slot (stage, c) of pair q at [(stage * 16 + c) *
+// (kThreads / 2) + q].  Lane 0 of a pair copies lambda and lambda', lane 1
+// psi and psi', while the previous item is computed.
+constexpr size_t kDirDfSmem = sizeof(float4) * 2 * 16 * (kThreads / 2);
+constexpr size_t kBaseDfSmem = sizeof(float4) * 2 * 8 * (kThreads / 2);
+
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 2) k_bwd_dir_df2(const BwdArgs a) {
     __shared__ float4 sg[16];
     __shared__ float4 sx[16];
+    extern __shared__ float4 stage_df[];
     const float4 *gate = reinterpret_cast<const float4 *>(a.gate);
     const float4 *dir = reinterpret_cast<const float4 *>(a.dir);
     if (threadIdx.x < 16) {
@@ -505,68 +525,98 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_dir_df2(const BwdArgs a) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) E[i] = czero();
     const int h = threadIdx.x & 1;
-    const long long Bm = (1LL << a.log2B) - 1;
-    const long long stride = ((long long)gridDim.x * blockDim.x) >> 1;
-    const long long start = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 1;
-    for (long long it = start; it < a.n_items; it += stride) {
-        const long long b = it & Bm, r = it >> a.log2B;
-        long long off[4];
-        if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
-        float4 l[4], dl[4], p[4], dp[4];
+    // the mask names only the pair, whose lanes always run the same iterations
+    const unsigned pair_mask = 0x3u << (threadIdx.x & 30);
+    float4 *mine = stage_df + (threadIdx.x >> 1);
+    const float4 *src0 = h ? psi : lam;
+    const float4 *src1 = h ? dpsi : reinterpret_cast<const float4 *>(dlam);
+    auto issue = [&](const long long (&o)[4], int st) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            l[c] = __ldg(&lam[off[c]]);
-            dl[c] = dlam[off[c]];
-            p[c] = __ldg(&psi[off[c]]);
-            dp[c] = __ldg(&dpsi[off[c]]);
+            cp_async16_f4(mine + (st * 16 + 8 * h + c) * (kThreads / 2), src0 + o[c]);
+            cp_async16_f4(mine + (st * 16 + 8 * h + 4 + c) * (kThreads / 2), src1 + o[c]);
         }
-        // both lanes of the pair have read dlam before either writes it; the mask
-        // names only the pair, whose lanes always run the same iterations
-        __syncwarp(0x3u << (threadIdx.x & 30));
+    };
+    const long long Bm = (1LL << a.log2B) - 1;
+    const long long stride = ((long long)gridDim.x * blockDim.x) >> 1;
+    long long it = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 1;
+    long long off[4], nxt[4];
+    bool ok = false;
+    if (it < a.n_items) {
+        ok = item_offsets4(a.geo, a.cols, it >> a.log2B, it & Bm, a.log2B, off);
+        if (ok) issue(off, 0);
+    }
+    cp_async_commit_df();
+    int st = 0;
+    for (; it < a.n_items; it += stride) {
+        __syncwarp(pair_mask);  // both lanes have read the stage about to be refilled
+        bool ok_next = false;
+        if (it + stride < a.n_items) {
+            ok_next = item_offsets4(a.geo, a.cols, (it + stride) >> a.log2B, (it + stride) & Bm, a.log2B, nxt);
+            if (ok_next) issue(nxt, st ^ 1);
+        }
+        cp_async_commit_df();
+        cp_async_wait_df<1>();
+        __syncwarp(pair_mask);  // the partner's copies of this item are visible
+        if (ok) {
+            float4 l[4], dl[4], p[4], dp[4];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const float4 li = h ? l[2 + u] : l[u];
-            const float4 dli = h ? dl[2 + u] : dl[u];
-            if (MODE == kGeneral) {
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    cmacc(E[u * 4 + c], dli, p[c]);
-                    cmacc(E[u * 4 + c], li, dp[c]);
-                }
-            } else {
-                const bool even = (h == 0) == (u == 0);
-                const float4 pa = even ? p[0] : p[1], pb = even ? p[3] : p[2];
-                const float4 qa = even ? dp[0] : dp[1], qb = even ? dp[3] : dp[2];
-                cmacc(E[u * 4 + 0], dli, pa);
-                cmacc(E[u * 4 + 0], li, qa);
-                cmacc(E[u * 4 + 1], dli, pb);
-                cmacc(E[u * 4 + 1], li, qb);
+            for (int c = 0; c < 4; ++c) {
+                l[c] = mine[(st * 16 + c) * (kThreads / 2)];
+                dl[c] = mine[(st * 16 + 4 + c) * (kThreads / 2)];
+                p[c] = mine[(st * 16 + 8 + c) * (kThreads / 2)];
+                dp[c] = mine[(st * 16 + 12 + c) * (kThreads / 2)];
             }
-        }
-        if (a.update) {
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                const int i = 2 * h + u;
-                CAcc q;
+                const float4 li = h ? l[2 + u] : l[u];
+                const float4 dli = h ? dl[2 + u] : dl[u];
                 if (MODE == kGeneral) {
-                    csetc(q, sg[0 * 4 + i], dl[0]);
 #pragma unroll
-                    for (int c = 1; c < 4; ++c) cmacc(q, sg[c * 4 + i], dl[c]);
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) cmacc(q, sx[c * 4 + i], l[c]);
+                    for (int c = 0; c < 4; ++c) {
+                        cmacc(E[u * 4 + c], dli, p[c]);
+                        cmacc(E[u * 4 + c], li, dp[c]);
+                    }
                 } else {
                     const bool even = (h == 0) == (u == 0);
-                    const int c0 = even ? 0 : 1, c1 = even ? 3 : 2;
-                    csetc(q, sg[c0 * 4 + i], even ? dl[0] : dl[1]);
-                    cmacc(q, sg[c1 * 4 + i], even ? dl[3] : dl[2]);
-                    cmacc(q, sx[c0 * 4 + i], even ? l[0] : l[1]);
-                    cmacc(q, sx[c1 * 4 + i], even ? l[3] : l[2]);
+                    const float4 pa = even ? p[0] : p[1], pb = even ? p[3] : p[2];
+                    const float4 qa = even ? dp[0] : dp[1], qb = even ? dp[3] : dp[2];
+                    cmacc(E[u * 4 + 0], dli, pa);
+                    cmacc(E[u * 4 + 0], li, qa);
+                    cmacc(E[u * 4 + 1], dli, pb);
+                    cmacc(E[u * 4 + 1], li, qb);
                 }
-                const long long oi = h ? off[2 + u] : off[u];
-                dlam[oi] = fin(q);
+            }
+            if (a.update) {
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int i = 2 * h + u;
+                    CAcc q;
+                    if (MODE == kGeneral) {
+                        csetc(q, sg[0 * 4 + i], dl[0]);
+#pragma unroll
+                        for (int c = 1; c < 4; ++c) cmacc(q, sg[c * 4 + i], dl[c]);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) cmacc(q, sx[c * 4 + i], l[c]);
+                    } else {
+                        const bool even = (h == 0) == (u == 0);
+                        const int c0 = even ? 0 : 1, c1 = even ? 3 : 2;
+                        csetc(q, sg[c0 * 4 + i], even ? dl[0] : dl[1]);
+                        cmacc(q, sg[c1 * 4 + i], even ? dl[3] : dl[2]);
+                        cmacc(q, sx[c0 * 4 + i], even ? l[0] : l[1]);
+                        cmacc(q, sx[c1 * 4 + i], even ? l[3] : l[2]);
+                    }
+                    const long long oi = h ? off[2 + u] : off[u];
+                    dlam[oi] = fin(q);
+                }
             }
         }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) off[c] = nxt[c];
+        ok = ok_next;
+        st ^= 1;
     }
+    cp_async_wait_df<0>();
     if (MODE != kGeneral) {
         // spread the block columns to their 4x4 positions: row 2h+u, columns c0, c1
 #pragma unroll
@@ -586,6 +636,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_dir_df2(const BwdArgs a) {
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 2) k_bwd_base_df2(const BwdArgs a) {
     __shared__ float4 sg[16];
+    extern __shared__ float4 stage_df[];  // [2][8][kThreads / 2]: lambda (lane 0), psi (lane 1)
     const float4 *gate = reinterpret_cast<const float4 *>(a.gate);
     if (threadIdx.x < 16) sg[threadIdx.x] = gate[threadIdx.x];
     __syncthreads();
@@ -596,56 +647,83 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_base_df2(const BwdArgs a) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) E[i] = czero();
     const int h = threadIdx.x & 1;
+    const unsigned pair_mask = 0x3u << (threadIdx.x & 30);
+    float4 *mine = stage_df + (threadIdx.x >> 1);
+    const float4 *src = h ? psi : reinterpret_cast<const float4 *>(lam);
+    const bool copies = h == 0 || accumulate;
+    auto issue = [&](const long long (&o)[4], int st) {
+        if (!copies) return;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cp_async16_f4(mine + (st * 8 + 4 * h + c) * (kThreads / 2), src + o[c]);
+    };
     const long long Bm = (1LL << a.log2B) - 1;
     const long long stride = ((long long)gridDim.x * blockDim.x) >> 1;
-    const long long start = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 1;
-    for (long long it = start; it < a.n_items; it += stride) {
-        const long long b = it & Bm, r = it >> a.log2B;
-        long long off[4];
-        if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
-        float4 l[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) l[c] = lam[off[c]];
-        // both lanes of the pair have read lambda before either writes it; the
-        // mask names only the pair, whose lanes always run the same iterations
-        __syncwarp(0x3u << (threadIdx.x & 30));
-        if (accumulate) {
-            float4 p[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) p[c] = __ldg(&psi[off[c]]);
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const float4 li = h ? l[2 + u] : l[u];
-                if (MODE == kGeneral) {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) cmacc(E[u * 4 + c], li, p[c]);
-                } else {
-                    const bool even = (h == 0) == (u == 0);
-                    cmacc(E[u * 4 + 0], li, even ? p[0] : p[1]);
-                    cmacc(E[u * 4 + 1], li, even ? p[3] : p[2]);
-                }
-            }
-        }
-        if (a.update) {
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int i = 2 * h + u;
-                CAcc q;
-                if (MODE == kGeneral) {
-                    csetc(q, sg[0 * 4 + i], l[0]);
-#pragma unroll
-                    for (int c = 1; c < 4; ++c) cmacc(q, sg[c * 4 + i], l[c]);
-                } else {
-                    const bool even = (h == 0) == (u == 0);
-                    const int c0 = even ? 0 : 1, c1 = even ? 3 : 2;
-                    csetc(q, sg[c0 * 4 + i], even ? l[0] : l[1]);
-                    cmacc(q, sg[c1 * 4 + i], even ? l[3] : l[2]);
-                }
-                const long long oi = h ? off[2 + u] : off[u];
-                lam[oi] = fin(q);
-            }
-        }
+    long long it = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 1;
+    long long off[4], nxt[4];
+    bool ok = false;
+    if (it < a.n_items) {
+        ok = item_offsets4(a.geo, a.cols, it >> a.log2B, it & Bm, a.log2B, off);
+        if (ok) issue(off, 0);
     }
+    cp_async_commit_df();
+    int st = 0;
+    for (; it < a.n_items; it += stride) {
+        __syncwarp(pair_mask);  // both lanes have read the stage about to be refilled
+        bool ok_next = false;
+        if (it + stride < a.n_items) {
+            ok_next = item_offsets4(a.geo, a.cols, (it + stride) >> a.log2B, (it + stride) & Bm, a.log2B, nxt);
+            if (ok_next) issue(nxt, st ^ 1);
+        }
+        cp_async_commit_df();
+        cp_async_wait_df<1>();
+        __syncwarp(pair_mask);  // the partner's copies of this item are visible
+        if (ok) {
+            float4 l[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) l[c] = mine[(st * 8 + c) * (kThreads / 2)];
+            if (accumulate) {
+                float4 p[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) p[c] = mine[(st * 8 + 4 + c) * (kThreads / 2)];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const float4 li = h ? l[2 + u] : l[u];
+                    if (MODE == kGeneral) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) cmacc(E[u * 4 + c], li, p[c]);
+                    } else {
+                        const bool even = (h == 0) == (u == 0);
+                        cmacc(E[u * 4 + 0], li, even ? p[0] : p[1]);
+                        cmacc(E[u * 4 + 1], li, even ? p[3] : p[2]);
+                    }
+                }
+            }
+            if (a.update) {
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int i = 2 * h + u;
+                    CAcc q;
+                    if (MODE == kGeneral) {
+                        csetc(q, sg[0 * 4 + i], l[0]);
+#pragma unroll
+                        for (int c = 1; c < 4; ++c) cmacc(q, sg[c * 4 + i], l[c]);
+                    } else {
+                        const bool even = (h == 0) == (u == 0);
+                        const int c0 = even ? 0 : 1, c1 = even ? 3 : 2;
+                        csetc(q, sg[c0 * 4 + i], even ? l[0] : l[1]);
+                        cmacc(q, sg[c1 * 4 + i], even ? l[3] : l[2]);
+                    }
+                    const long long oi = h ? off[2 + u] : off[u];
+                    lam[oi] = fin(q);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) off[c] = nxt[c];
+        ok = ok_next;
+        st ^= 1;
+    }
+    cp_async_wait_df<0>();
     if (!accumulate) return;
     if (MODE != kGeneral) {
 #pragma unroll
@@ -725,18 +803,27 @@ void launch_fwd_df64(const FwdArgs &a, int grid, cudaStream_t s) {
 
 void launch_bwd_base_df64(const BwdArgs &a, int grid, cudaStream_t s) {
     switch (a.geo.mode) {
-        case kGeneral: k_bwd_base_df2<kGeneral><<<grid, kThreads, 0, s>>>(a); break;
-        case kParity4: k_bwd_base_df2<kParity4><<<grid, kThreads, 0, s>>>(a); break;
+        case kGeneral: k_bwd_base_df2<kGeneral><<<grid, kThreads, kBaseDfSmem, s>>>(a); break;
+        case kParity4: k_bwd_base_df2<kParity4><<<grid, kThreads, kBaseDfSmem, s>>>(a); break;
         default: k_bwd_base_df<kParity2><<<grid, kThreads, 0, s>>>(a); break;
     }
 }
 
 void launch_bwd_dir_df64(const BwdArgs &a, int grid, cudaStream_t s) {
     switch (a.geo.mode) {
-        case kGeneral: k_bwd_dir_df2<kGeneral><<<grid, kThreads, 0, s>>>(a); break;
-        case kParity4: k_bwd_dir_df2<kParity4><<<grid, kThreads, 0, s>>>(a); break;
+        case kGeneral: k_bwd_dir_df2<kGeneral><<<grid, kThreads, kDirDfSmem, s>>>(a); break;
+        case kParity4: k_bwd_dir_df2<kParity4><<<grid, kThreads, kDirDfSmem, s>>>(a); break;
         default: k_bwd_dir_df<kParity2><<<grid, kThreads, 0, s>>>(a); break;
     }
+}
+
+cudaError_t init_sweep_attributes_df64() {
+    cudaError_t e = cudaFuncSetAttribute(k_bwd_dir_df2<kGeneral>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kDirDfSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_bwd_dir_df2<kParity4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kDirDfSmem);
+    return e;
 }
 
 void launch_init_unit_df64(double2 *psi0, const int32_t *cols, int B, int log2B, long long n_store,
