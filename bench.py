@@ -425,12 +425,15 @@ def run_ours(args):
         ctx.close()
         return out
 
-    def measure_sweeps():
-        """Gradient time per basis summand (the paper's Fig. matchgate_gradient):
-        spinful chains with 5 layers for n = 6..16, and n = 10 for 1..21 layers;
-        FP64, general gates.  Each point: one warm-up gradient, then the median
-        of three timed gradients over min(2^n, 4096) columns, divided by the
-        number of columns."""
+    def measure_sweeps(inits: int = 20):
+        """Gradient time per basis summand (the paper's Fig. matchgate_gradient
+        and its scaling shapes): spinful chains with 5 layers for n = 6..16,
+        n = 10 for 1..21 layers, and the shapes n = 10 / 11 layers, n = 12 /
+        3 layers, n = 16 / 11 layers.  FP64, general gates, f + Riemannian
+        gradient through the host C-ABI call (`rq_grad`, pinned host gates).
+        Each point: `inits` random initialisations (seeded Haar gates), one
+        gradient each over min(2^n, 4096) columns after a warm-up; the median
+        time divided by the number of columns."""
         def point(L, depth):
             prob = w.make_problem(L, depth, 0.5, seed=900 + L * 31 + depth)
             ctx = rq.Context(local).setup_problem(prob)
@@ -438,15 +441,19 @@ def run_ours(args):
             ctx.set_columns(0, ncols)
             ctx.grad(prob.gates)
             ts = []
-            for _ in range(3):
+            for i in range(inits):
+                gates = np.stack([w.random_unitary(4, 7000 + 97 * i + p) for p in range(prob.n_params)])
+                g_h = torch.from_numpy(gates).pin_memory().numpy()
                 t0 = time.perf_counter()
-                ctx.grad(prob.gates)
+                ctx.grad(g_h)
                 ts.append(time.perf_counter() - t0)
             ctx.close()
-            return {"n": prob.n, "layers": depth, "gates": prob.n_gates, "columns": ncols,
-                    "s_per_summand": float(np.median(ts)) / ncols}
+            med = float(np.median(ts))
+            return {"n": prob.n, "layers": depth, "gates": prob.n_gates, "columns": ncols, "inits": inits,
+                    "s_per_summand": med / ncols, "s_per_gradient_full_basis": med * (1 << prob.n) / ncols}
         return {"vs_qubits_5_layers": [point(L, 5) for L in (3, 4, 5, 6, 7, 8)],
-                "vs_layers_10_qubits": [point(5, d) for d in (1, 3, 5, 7, 9, 11, 15, 21)]}
+                "vs_layers_10_qubits": [point(5, d) for d in (1, 3, 5, 7, 9, 11, 15, 21)],
+                "shapes": [point(5, 11), point(6, 3), point(8, 11)]}
 
     if args.parity_only:   # profiling cases only: the parity-gate sweep alone
         par = measure(1, args.steps, args.warmup, args.tile)
