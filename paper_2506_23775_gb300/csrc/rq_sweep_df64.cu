@@ -183,14 +183,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_fwd_df(const FwdArgs a) {
         if (MODE == kGeneral || MODE == kParity4) {
             long long off[4];
             if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
-            // the first tangent's loads are issued with the state's, before any
-            // store, so both latencies overlap
-            float4 p[4], t[4];
+            float4 p[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                p[c] = __ldg(&psi_in[off[c]]);
-                if (a.kdirs > 0) t[c] = __ldg(&dpsi_in[off[c]]);
-            }
+            for (int c = 0; c < 4; ++c) p[c] = __ldg(&psi_in[off[c]]);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 CAcc q;
@@ -207,10 +202,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_fwd_df(const FwdArgs a) {
             for (int d = 0; d < a.kdirs; ++d) {
                 const float4 *din = dpsi_in + d * a.dir_stride;
                 float4 *dout = dpsi_out + d * a.dir_stride;
-                if (d > 0) {
+                float4 t[4];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) t[c] = __ldg(&din[off[c]]);
-                }
+                for (int c = 0; c < 4; ++c) t[c] = __ldg(&din[off[c]]);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     CAcc q;

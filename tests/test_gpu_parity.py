@@ -173,6 +173,22 @@ def test_invalid_arguments(rq):
         ctx.set_tile(3, 1)
 
 
+def test_size_limits(rq):
+    """n = 20 (10 sites) is within the qubit limit, but the target's sector
+    blocks alone would need C(20,10)^2 x 16 B = 546 GB: set-up fails with
+    RQ_ENOMEM and the context stays usable; n = 22 is past the limit."""
+    ctx = rq.Context(0)
+    with pytest.raises(rq.RQError) as e:
+        ctx.setup_problem(w.make_problem(10, 1, 0.5, seed=3))
+    assert e.value.code == rq.RQ_ENOMEM
+    with pytest.raises(rq.RQError) as e:
+        ctx.setup_problem(w.make_problem(11, 1, 0.5, seed=3))
+    assert e.value.code == rq.RQ_EINVAL
+    prob = w.config_problem("small")
+    ref = _ctx(rq, prob).cost(prob.gates)
+    assert ctx.setup_problem(prob).cost(prob.gates) == ref
+
+
 def test_device_pointer_variants_match_host(rq):
     torch = pytest.importorskip("torch")
     prob = w.config_problem("small")
