@@ -160,7 +160,12 @@ rq_status rq_set_columns(rq_ctx *ctx, int64_t col_begin, int64_t col_end);
 
 /* Tuning: columns per tile (a power of two, 0 = automatic) and the number of
  * HVP directions swept together (1..4, 0 = automatic).  Reallocates the
- * workspace; RQ_ENOMEM if it does not fit. */
+ * workspace; RQ_ENOMEM if it does not fit.  Directions beyond max_dirs are
+ * swept in further chunks, each repeating the forward and adjoint sweeps;
+ * the automatic choice keeps tiles of at least 256 columns, which at n = 16
+ * means one direction per sweep, so callers that evaluate k > 1 directions
+ * per call should pass max_dirs = k (e.g. 128 columns x 4 directions at
+ * n = 16: 25 % less work per 4-direction evaluation than 4 chunks). */
 rq_status rq_set_tile(rq_ctx *ctx, int columns_per_tile, int max_dirs);
 
 /* Full Hessian (paper Sec. "Efficient gradient and Hessian computation",
