@@ -1165,7 +1165,9 @@ rq_status rq_setup_target(rq_ctx *ctx, const rq_target *tgt, const rq_circuit *c
     ctx->param_of.resize(ctx->g);
     for (int l = 0; l < ctx->g; ++l) ctx->param_of[l] = c->param_of ? c->param_of[l] : l;
     ctx->n_store = ctx->structure == 1 ? (1LL << (ctx->n - 1)) : (1LL << ctx->n);
-    ctx->geo.resize(ctx->g);
+    // every field of every gate is reset: a previous problem's first-layer
+    // masks must not survive into this one
+    ctx->geo.assign(ctx->g, GateGeom{});
     for (int l = 0; l < ctx->g; ++l) {
         const int a = ctx->pairs[2 * l], b = ctx->pairs[2 * l + 1], n = ctx->n;
         GateGeom &gg = ctx->geo[l];
