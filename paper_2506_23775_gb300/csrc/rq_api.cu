@@ -220,6 +220,11 @@ void free_small(rq_ctx *ctx) {
     ctx->small_bytes = 0;
 }
 
+// The tile workspace exists (a failed reallocation leaves it released).
+bool workspace_ok(const rq_ctx *ctx) {
+    return ctx->d_psi && ctx->d_dpsi && ctx->d_lam && ctx->d_dlam && ctx->d_part && ctx->d_partd && ctx->d_fpart;
+}
+
 void drop_graphs(rq_ctx *ctx) {
     for (auto &e : ctx->graphs)
         if (e.exec) cudaGraphExecDestroy(e.exec);
@@ -661,6 +666,9 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
     if (misaligned(gates) || (k > 0 && misaligned(dirs)) || (rgrad && misaligned(rgrad)) || (hvps && misaligned(hvps)))
         return fail(ctx, RQ_EINVAL, "gates, dirs, rgrad and hvps must be 16-byte aligned device pointers");
     RQ_TRY(ensure_small(ctx, k));
+    if (!workspace_ok(ctx))
+        return fail(ctx, RQ_ESTATE, "the sweep workspace is not allocated (a previous tile, column-range or "
+                    "checkpointing change failed): set the tile again");
     cudaStream_t s = ctx->stream;
     const int g = ctx->g, P = ctx->P;
     {
@@ -1269,6 +1277,8 @@ rq_status rq_hessian(rq_ctx *ctx, const double *gates, double *f, double *egrad,
                     "gates: set the checkpoint interval to 1 (a smaller tile if memory is short)", ctx->ckpt_r);
     RQ_TRY(rq::check_gates(ctx, gates));
     RQ_TRY(ensure_small(ctx, 1));
+    if (!workspace_ok(ctx))
+        return fail(ctx, RQ_ESTATE, "the sweep workspace is not allocated (a previous tile change failed)");
     cudaStream_t s = ctx->stream;
     const int g = ctx->g, P = ctx->P, B = ctx->B;
     const int log2M = ctx->structure == 1 ? 3 : 4, M = 1 << log2M;
