@@ -176,11 +176,12 @@ __device__ __forceinline__ void env3_finish(const double (&K1)[16], const double
 
 // ------------------------------------------------ pipelined item loads --
 //
-// The general-gate backward kernels hold ~210 registers, so an SM runs only
+// The general-gate backward kernels hold ~200 registers, so an SM runs only
 // eight of their warps; while a warp waits for its item's amplitudes from
-// HBM, the FP64 pipe depends on the others.  Their grid-stride loops
-// therefore copy the next item's amplitudes into this thread's own slots of
-// shared memory (cp.async, two stages) while the current item is computed.
+// HBM, the FP64 pipe depends on the others.  Their grid-stride loops (and
+// that of the parity-gate base step) therefore copy the next item's
+// amplitudes into this thread's own slots of shared memory (cp.async, two
+// stages) while the current item is computed.
 // Slot (stage, c) of thread t is at [(stage * NA + c) * kThreads + t], so a
 // warp's copies and reads of one slot are contiguous.
 
@@ -404,7 +405,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_base(const BwdArgs a) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) K1[i] = K2[i] = K3[i] = 0.0;
     const long long Bm = (1LL << a.log2B) - 1;
-    if constexpr (MODE == kGeneral) {
+    if constexpr (MODE == kGeneral || MODE == kParity4) {
+        // gates on two stored qubits: pipelined item loads
         extern __shared__ double2 pf[];
         double2 *mine = pf + threadIdx.x;
         auto slot = [&](int st, int c) { return mine + (st * kBaseSlots + c) * kThreads; };
@@ -421,52 +423,50 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_base(const BwdArgs a) {
                 }
             },
             [&](const long long (&off)[4], int st) {
-                Amp3 l[4];
+                if constexpr (MODE == kGeneral) {
+                    Amp3 l[4];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) l[c] = amp3(*slot(st, c));
-                if (accumulate) {
-                    Amp3 p[4];
+                    for (int c = 0; c < 4; ++c) l[c] = amp3(*slot(st, c));
+                    if (accumulate) {
+                        Amp3 p[4];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) p[c] = amp3(*slot(st, 4 + c));
-                    env3(K1, K2, K3, l, p);
-                }
-                if (a.update) {
-                    double2 q[4];
-                    matvec3(sgT3, l, q);
+                        for (int c = 0; c < 4; ++c) p[c] = amp3(*slot(st, 4 + c));
+                        env3(K1, K2, K3, l, p);
+                    }
+                    if (a.update) {
+                        double2 q[4];
+                        matvec3(sgT3, l, q);
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) a.lam[off[c]] = q[c];
+                        for (int c = 0; c < 4; ++c) a.lam[off[c]] = q[c];
+                    }
+                } else {
+                    double2 l[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) l[c] = *slot(st, c);
+                    if (accumulate) {
+                        double2 p[4];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) p[c] = *slot(st, 4 + c);
+                        cmacc(E[0], l[0], p[0]); cmacc(E[3], l[0], p[3]);
+                        cmacc(E[12], l[3], p[0]); cmacc(E[15], l[3], p[3]);
+                        cmacc(E[5], l[1], p[1]); cmacc(E[6], l[1], p[2]);
+                        cmacc(E[9], l[2], p[1]); cmacc(E[10], l[2], p[2]);
+                    }
+                    if (a.update) {
+                        double2 q[4];
+                        q[0] = zero2(); cmacc(q[0], sg[0], l[0]); cmacc(q[0], sg[12], l[3]);
+                        q[3] = zero2(); cmacc(q[3], sg[3], l[0]); cmacc(q[3], sg[15], l[3]);
+                        q[1] = zero2(); cmacc(q[1], sg[5], l[1]); cmacc(q[1], sg[9], l[2]);
+                        q[2] = zero2(); cmacc(q[2], sg[6], l[1]); cmacc(q[2], sg[10], l[2]);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) a.lam[off[c]] = q[c];
+                    }
                 }
             });
-    }
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; MODE != kGeneral && it < a.n_items;
-         it += stride) {
-        const long long b = it & Bm, r = it >> a.log2B;
-        if constexpr (MODE == kParity4) {
-            long long off[4];
-            if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
-            double2 l[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) l[c] = a.lam[off[c]];
-            if (accumulate) {
-                double2 p[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) p[c] = __ldg(&a.psi[off[c]]);
-                cmacc(E[0], l[0], p[0]); cmacc(E[3], l[0], p[3]);
-                cmacc(E[12], l[3], p[0]); cmacc(E[15], l[3], p[3]);
-                cmacc(E[5], l[1], p[1]); cmacc(E[6], l[1], p[2]);
-                cmacc(E[9], l[2], p[1]); cmacc(E[10], l[2], p[2]);
-            }
-            if (a.update) {
-                double2 q[4];
-                q[0] = zero2(); cmacc(q[0], sg[0], l[0]); cmacc(q[0], sg[12], l[3]);
-                q[3] = zero2(); cmacc(q[3], sg[3], l[0]); cmacc(q[3], sg[15], l[3]);
-                q[1] = zero2(); cmacc(q[1], sg[5], l[1]); cmacc(q[1], sg[9], l[2]);
-                q[2] = zero2(); cmacc(q[2], sg[6], l[1]); cmacc(q[2], sg[10], l[2]);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) a.lam[off[c]] = q[c];
-            }
-        } else {  // kParity2
+    } else {  // kParity2: two-amplitude items, plain loads
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.n_items; it += stride) {
+            const long long b = it & Bm, r = it >> a.log2B;
             long long off[2];
             int i0, i1;
             offsets2(r, b, a.geo.pa, a.geo.qfirst, a.tile_parity, a.log2B, off, i0, i1);
@@ -567,72 +567,72 @@ __global__ void __launch_bounds__(kThreads, MODE == kGeneral ? 1 : 2) k_bwd_dir(
                     for (int c = 0; c < 4; ++c) a.dlam[off[c]] = q[c];
                 }
             });
-    }
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; MODE != kGeneral && it < a.n_items;
-         it += stride) {
-        const long long b = it & Bm, r = it >> a.log2B;
-        if constexpr (MODE == kParity4) {
-            long long off[4];
-            if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
-            double2 l[4], dl[4], p[4], dp[4];
+    } else {  // parity gates: plain loads (two CTAs per SM cover their latency)
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.n_items; it += stride) {
+            const long long b = it & Bm, r = it >> a.log2B;
+            if constexpr (MODE == kParity4) {
+                long long off[4];
+                if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
+                double2 l[4], dl[4], p[4], dp[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                l[c] = __ldg(&a.lam[off[c]]);
-                dl[c] = a.dlam[off[c]];
-                p[c] = __ldg(&a.psi[off[c]]);
-                dp[c] = __ldg(&a.dpsi[off[c]]);
-            }
-            const int idx[8][2] = {{0, 0}, {0, 3}, {3, 0}, {3, 3}, {1, 1}, {1, 2}, {2, 1}, {2, 2}};
+                for (int c = 0; c < 4; ++c) {
+                    l[c] = __ldg(&a.lam[off[c]]);
+                    dl[c] = a.dlam[off[c]];
+                    p[c] = __ldg(&a.psi[off[c]]);
+                    dp[c] = __ldg(&a.dpsi[off[c]]);
+                }
+                const int idx[8][2] = {{0, 0}, {0, 3}, {3, 0}, {3, 3}, {1, 1}, {1, 2}, {2, 1}, {2, 2}};
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                cmacc(E[idx[u][0] * 4 + idx[u][1]], dl[idx[u][0]], p[idx[u][1]]);
-                cmacc(E[idx[u][0] * 4 + idx[u][1]], l[idx[u][0]], dp[idx[u][1]]);
-            }
-            if (a.update) {
-                double2 q[4];
-                q[0] = zero2(); cmacc(q[0], sg[0], dl[0]); cmacc(q[0], sg[12], dl[3]);
-                cmacc(q[0], sx[0], l[0]); cmacc(q[0], sx[12], l[3]);
-                q[3] = zero2(); cmacc(q[3], sg[3], dl[0]); cmacc(q[3], sg[15], dl[3]);
-                cmacc(q[3], sx[3], l[0]); cmacc(q[3], sx[15], l[3]);
-                q[1] = zero2(); cmacc(q[1], sg[5], dl[1]); cmacc(q[1], sg[9], dl[2]);
-                cmacc(q[1], sx[5], l[1]); cmacc(q[1], sx[9], l[2]);
-                q[2] = zero2(); cmacc(q[2], sg[6], dl[1]); cmacc(q[2], sg[10], dl[2]);
-                cmacc(q[2], sx[6], l[1]); cmacc(q[2], sx[10], l[2]);
+                for (int u = 0; u < 8; ++u) {
+                    cmacc(E[idx[u][0] * 4 + idx[u][1]], dl[idx[u][0]], p[idx[u][1]]);
+                    cmacc(E[idx[u][0] * 4 + idx[u][1]], l[idx[u][0]], dp[idx[u][1]]);
+                }
+                if (a.update) {
+                    double2 q[4];
+                    q[0] = zero2(); cmacc(q[0], sg[0], dl[0]); cmacc(q[0], sg[12], dl[3]);
+                    cmacc(q[0], sx[0], l[0]); cmacc(q[0], sx[12], l[3]);
+                    q[3] = zero2(); cmacc(q[3], sg[3], dl[0]); cmacc(q[3], sg[15], dl[3]);
+                    cmacc(q[3], sx[3], l[0]); cmacc(q[3], sx[15], l[3]);
+                    q[1] = zero2(); cmacc(q[1], sg[5], dl[1]); cmacc(q[1], sg[9], dl[2]);
+                    cmacc(q[1], sx[5], l[1]); cmacc(q[1], sx[9], l[2]);
+                    q[2] = zero2(); cmacc(q[2], sg[6], dl[1]); cmacc(q[2], sg[10], dl[2]);
+                    cmacc(q[2], sx[6], l[1]); cmacc(q[2], sx[10], l[2]);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) a.dlam[off[c]] = q[c];
-            }
-        } else {  // kParity2
-            long long off[2];
-            int i0, i1;
-            offsets2(r, b, a.geo.pa, a.geo.qfirst, a.tile_parity, a.log2B, off, i0, i1);
-            const double2 l0 = __ldg(&a.lam[off[0]]), l1 = __ldg(&a.lam[off[1]]);
-            const double2 d0 = a.dlam[off[0]], d1 = a.dlam[off[1]];
-            const double2 p0 = __ldg(&a.psi[off[0]]), p1 = __ldg(&a.psi[off[1]]);
-            const double2 t0 = __ldg(&a.dpsi[off[0]]), t1 = __ldg(&a.dpsi[off[1]]);
-            double2 c00 = zero2(), c01 = zero2(), c10 = zero2(), c11 = zero2();
-            cmacc(c00, d0, p0); cmacc(c00, l0, t0);
-            cmacc(c01, d0, p1); cmacc(c01, l0, t1);
-            cmacc(c10, d1, p0); cmacc(c10, l1, t0);
-            cmacc(c11, d1, p1); cmacc(c11, l1, t1);
-            if (i0 == 0) {
-                E[0].x += c00.x; E[0].y += c00.y; E[3].x += c01.x; E[3].y += c01.y;
-                E[12].x += c10.x; E[12].y += c10.y; E[15].x += c11.x; E[15].y += c11.y;
-            } else if (i0 == 1) {
-                E[5].x += c00.x; E[5].y += c00.y; E[6].x += c01.x; E[6].y += c01.y;
-                E[9].x += c10.x; E[9].y += c10.y; E[10].x += c11.x; E[10].y += c11.y;
-            } else {
-                E[10].x += c00.x; E[10].y += c00.y; E[9].x += c01.x; E[9].y += c01.y;
-                E[6].x += c10.x; E[6].y += c10.y; E[5].x += c11.x; E[5].y += c11.y;
-            }
-            if (a.update) {
-                double2 q0 = zero2(), q1 = zero2();
-                cmacc(q0, sg[i0 * 4 + i0], d0); cmacc(q0, sg[i1 * 4 + i0], d1);
-                cmacc(q0, sx[i0 * 4 + i0], l0); cmacc(q0, sx[i1 * 4 + i0], l1);
-                cmacc(q1, sg[i0 * 4 + i1], d0); cmacc(q1, sg[i1 * 4 + i1], d1);
-                cmacc(q1, sx[i0 * 4 + i1], l0); cmacc(q1, sx[i1 * 4 + i1], l1);
-                a.dlam[off[0]] = q0;
-                a.dlam[off[1]] = q1;
+                    for (int c = 0; c < 4; ++c) a.dlam[off[c]] = q[c];
+                }
+            } else {  // kParity2
+                long long off[2];
+                int i0, i1;
+                offsets2(r, b, a.geo.pa, a.geo.qfirst, a.tile_parity, a.log2B, off, i0, i1);
+                const double2 l0 = __ldg(&a.lam[off[0]]), l1 = __ldg(&a.lam[off[1]]);
+                const double2 d0 = a.dlam[off[0]], d1 = a.dlam[off[1]];
+                const double2 p0 = __ldg(&a.psi[off[0]]), p1 = __ldg(&a.psi[off[1]]);
+                const double2 t0 = __ldg(&a.dpsi[off[0]]), t1 = __ldg(&a.dpsi[off[1]]);
+                double2 c00 = zero2(), c01 = zero2(), c10 = zero2(), c11 = zero2();
+                cmacc(c00, d0, p0); cmacc(c00, l0, t0);
+                cmacc(c01, d0, p1); cmacc(c01, l0, t1);
+                cmacc(c10, d1, p0); cmacc(c10, l1, t0);
+                cmacc(c11, d1, p1); cmacc(c11, l1, t1);
+                if (i0 == 0) {
+                    E[0].x += c00.x; E[0].y += c00.y; E[3].x += c01.x; E[3].y += c01.y;
+                    E[12].x += c10.x; E[12].y += c10.y; E[15].x += c11.x; E[15].y += c11.y;
+                } else if (i0 == 1) {
+                    E[5].x += c00.x; E[5].y += c00.y; E[6].x += c01.x; E[6].y += c01.y;
+                    E[9].x += c10.x; E[9].y += c10.y; E[10].x += c11.x; E[10].y += c11.y;
+                } else {
+                    E[10].x += c00.x; E[10].y += c00.y; E[9].x += c01.x; E[9].y += c01.y;
+                    E[6].x += c10.x; E[6].y += c10.y; E[5].x += c11.x; E[5].y += c11.y;
+                }
+                if (a.update) {
+                    double2 q0 = zero2(), q1 = zero2();
+                    cmacc(q0, sg[i0 * 4 + i0], d0); cmacc(q0, sg[i1 * 4 + i0], d1);
+                    cmacc(q0, sx[i0 * 4 + i0], l0); cmacc(q0, sx[i1 * 4 + i0], l1);
+                    cmacc(q1, sg[i0 * 4 + i1], d0); cmacc(q1, sg[i1 * 4 + i1], d1);
+                    cmacc(q1, sx[i0 * 4 + i1], l0); cmacc(q1, sx[i1 * 4 + i1], l1);
+                    a.dlam[off[0]] = q0;
+                    a.dlam[off[1]] = q1;
+                }
             }
         }
     }
@@ -663,7 +663,7 @@ void launch_fwd(const FwdArgs &a, int grid, cudaStream_t s) {
 void launch_bwd_base(const BwdArgs &a, int grid, cudaStream_t s) {
     switch (a.geo.mode) {
         case kGeneral: k_bwd_base<kGeneral><<<grid, kThreads, kBaseSmem, s>>>(a); break;
-        case kParity4: k_bwd_base<kParity4><<<grid, kThreads, 0, s>>>(a); break;
+        case kParity4: k_bwd_base<kParity4><<<grid, kThreads, kBaseSmem, s>>>(a); break;
         default: k_bwd_base<kParity2><<<grid, kThreads, 0, s>>>(a); break;
     }
 }
@@ -677,12 +677,14 @@ void launch_bwd_dir(const BwdArgs &a, int grid, cudaStream_t s) {
 }
 
 cudaError_t init_sweep_attributes() {
-    // the pipelined general-gate kernels keep two stages of item slots in
-    // dynamic shared memory (128 KB and 64 KB per CTA)
+    // the pipelined kernels keep two stages of item slots in dynamic shared
+    // memory (128 KB per CTA for k_bwd_dir, 64 KB for k_bwd_base)
     cudaError_t e = cudaFuncSetAttribute(k_bwd_dir<kGeneral>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kDirSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_bwd_base<kGeneral>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBaseSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_bwd_base<kParity4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBaseSmem);
     return e;
 }
 
