@@ -41,8 +41,8 @@ HBM_FALLBACK_GBS = 6800.0
 # workload (2^14 x 512 items: n = 16, general gates, 512-column tile):
 # dram__bytes_read.sum + dram__bytes_write.sum of the same kernel captured at
 # n = 14 (2^12 x 512 items: 536.93 + 112.18 MB) scaled by the items, 4x; the
-# reads of 2^12 x 256 items are exactly half (profiles/
-# bwd_gate_dir_dram_traffic.md).  Algorithmic bytes of that launch:
+# reads of 2^12 x 256 items are exactly half (the DRAM-traffic ncu summary
+# under profiles/).  Algorithmic bytes of that launch:
 # 2^14 * 512 * 5 * 4 * 16 = 2.684e9.  The figure holds only for the kernel
 # source it was taken on, so the sources are hashed and compared at run time.
 TRAFFIC = {"kernel": "bwd_gate_dir", "bytes_per_launch": 2596414464,
