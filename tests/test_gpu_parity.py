@@ -189,6 +189,25 @@ def test_size_limits(rq):
     assert ctx.setup_problem(prob).cost(prob.gates) == ref
 
 
+def test_context_reuse_across_problems(rq):
+    """One context set up for several problems in turn gives exactly what a
+    fresh context gives for each (no per-problem state survives a set-up)."""
+    seq = [w.config_problem("n14"), w.config_problem("small"), w.config_problem("tied12"),
+           w.config_problem("small", structure=1), w.make_problem(5, 4, 0.3, seed=8, periodic=True)]
+    ctx = rq.Context(0)
+    for prob in seq:
+        X = w.random_directions(prob.n_params, 2, 17)
+        cols = (0, min(1 << prob.n, 600))
+        ctx.setup_problem(prob)
+        ctx.set_columns(*cols)
+        got = ctx.hvp(prob.gates, X)
+        fresh = _ctx(rq, prob)
+        fresh.set_columns(*cols)
+        ref = fresh.hvp(prob.gates, X)
+        assert got[0] == ref[0]
+        assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2])
+
+
 def test_device_pointer_variants_match_host(rq):
     torch = pytest.importorskip("torch")
     prob = w.config_problem("small")
