@@ -369,7 +369,9 @@ rq_status rebuild_tiles_impl(rq_ctx *ctx) {
         return fail(ctx, RQ_ENOMEM, "one column needs %lld bytes of workspace, %.0f available",
                     bytes_per_column(ctx, 1), budget);
     const long long items = std::max<long long>(1, ctx->n_store / 4 * B);
-    const int ncta = (int)std::min<long long>((long long)ctx->sms * rq::kCtasPerSm, (items + rq::kThreads - 1) / rq::kThreads);
+    // at least one warp-sized chunk of items per CTA: small sweeps spread over
+    // every SM (the sweep kernels hand chunks to CTAs round robin)
+    const int ncta = (int)std::min<long long>((long long)ctx->sms * rq::kCtasPerSm, (items + 31) / 32);
     std::vector<int32_t> cols;
     std::vector<double> wts;
     std::vector<int> tpar;

@@ -9,6 +9,22 @@
 
 namespace rq {
 
+// First item of this thread in a grid-stride sweep over items (stride
+// gridDim.x * blockDim.x): the lanes of a warp take 32 consecutive items
+// (coalesced rows), and consecutive warp-sized chunks go to different CTAs
+// before they go to the next warp of a CTA, so a sweep with few items still
+// reaches every SM.  Chunk w * gridDim.x + blockIdx.x of warp w: a bijection
+// onto [0, gridDim.x * blockDim.x).
+__device__ __forceinline__ long long first_item() {
+    return ((long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
+}
+
+// The same for two lanes per item (16 items per warp chunk; stride
+// gridDim.x * blockDim.x / 2).
+__device__ __forceinline__ long long first_pair_item() {
+    return ((long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 16 + ((threadIdx.x & 31) >> 1);
+}
+
 // r with a zero bit inserted at position p
 __device__ __forceinline__ long long insert_zero(long long r, int p) {
     const long long lo = r & ((1LL << p) - 1);

@@ -207,7 +207,7 @@ constexpr size_t kBaseSmem = sizeof(double2) * 2 * kBaseSlots * kThreads;
 template <class Offsets, class Issue, class Body>
 __device__ __forceinline__ void pipelined_items(long long n_items, Offsets offsets, Issue issue, Body body) {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long it = first_item();
     long long off[4], nxt[4];
     bool ok = false;
     if (it < n_items) {
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fwd(const FwdArgs a) {
     __syncthreads();
     const long long Bm = (1LL << a.log2B) - 1;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.n_items; it += stride) {
+    for (long long it = first_item(); it < a.n_items; it += stride) {
         const long long b = it & Bm, r = it >> a.log2B;
         if constexpr (MODE == kGeneral) {
             long long off[4];
@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_base(const BwdArgs a) {
             });
     } else {  // kParity2: two-amplitude items, plain loads
         const long long stride = (long long)gridDim.x * blockDim.x;
-        for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.n_items; it += stride) {
+        for (long long it = first_item(); it < a.n_items; it += stride) {
             const long long b = it & Bm, r = it >> a.log2B;
             long long off[2];
             int i0, i1;
@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kGeneral ? 1 : 2) k_bwd_dir(
             });
     } else {  // parity gates: plain loads (two CTAs per SM cover their latency)
         const long long stride = (long long)gridDim.x * blockDim.x;
-        for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.n_items; it += stride) {
+        for (long long it = first_item(); it < a.n_items; it += stride) {
             const long long b = it & Bm, r = it >> a.log2B;
             if constexpr (MODE == kParity4) {
                 long long off[4];

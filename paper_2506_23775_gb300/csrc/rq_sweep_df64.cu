@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fwd_df(const FwdArgs a) {
     float4 *dpsi_out = reinterpret_cast<float4 *>(a.dpsi_out);
     const long long Bm = (1LL << a.log2B) - 1;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.n_items; it += stride) {
+    for (long long it = first_item(); it < a.n_items; it += stride) {
         const long long b = it & Bm, r = it >> a.log2B;
         if (MODE == kGeneral || MODE == kParity4) {
             long long off[4];
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_base_df(const BwdArgs a) {
     for (int i = 0; i < 16; ++i) E[i] = czero();
     const long long Bm = (1LL << a.log2B) - 1;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.n_items; it += stride) {
+    for (long long it = first_item(); it < a.n_items; it += stride) {
         const long long b = it & Bm, r = it >> a.log2B;
         if (MODE == kGeneral || MODE == kParity4) {
             long long off[4];
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_dir_df(const BwdArgs a) {
     for (int i = 0; i < 16; ++i) E[i] = czero();
     const long long Bm = (1LL << a.log2B) - 1;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.n_items; it += stride) {
+    for (long long it = first_item(); it < a.n_items; it += stride) {
         const long long b = it & Bm, r = it >> a.log2B;
         if (MODE == kGeneral || MODE == kParity4) {
             long long off[4];
@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_dir_df2(const BwdArgs a) {
     };
     const long long Bm = (1LL << a.log2B) - 1;
     const long long stride = ((long long)gridDim.x * blockDim.x) >> 1;
-    long long it = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 1;
+    long long it = first_pair_item();
     long long off[4], nxt[4];
     bool ok = false;
     if (it < a.n_items) {
@@ -658,7 +658,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_base_df2(const BwdArgs a) {
     };
     const long long Bm = (1LL << a.log2B) - 1;
     const long long stride = ((long long)gridDim.x * blockDim.x) >> 1;
-    long long it = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 1;
+    long long it = first_pair_item();
     long long off[4], nxt[4];
     bool ok = false;
     if (it < a.n_items) {
