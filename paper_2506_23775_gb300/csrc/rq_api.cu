@@ -369,9 +369,14 @@ rq_status rebuild_tiles_impl(rq_ctx *ctx) {
         return fail(ctx, RQ_ENOMEM, "one column needs %lld bytes of workspace, %.0f available",
                     bytes_per_column(ctx, 1), budget);
     const long long items = std::max<long long>(1, ctx->n_store / 4 * B);
-    // at least one warp-sized chunk of items per CTA: small sweeps spread over
-    // every SM (the sweep kernels hand chunks to CTAs round robin)
-    const int ncta = (int)std::min<long long>((long long)ctx->sms * rq::kCtasPerSm, (items + 31) / 32);
+    // Sweeps with a full block of items for every CTA: two CTAs per SM.
+    // Smaller sweeps: one CTA per SM at most (the general backward kernels fit
+    // one CTA per SM, so more would run in two waves), and at least one
+    // warp-sized chunk of items per CTA (the kernels hand chunks to CTAs round
+    // robin, so a small sweep still reaches every SM).
+    const long long full = (long long)ctx->sms * rq::kCtasPerSm * rq::kThreads;
+    const int ncta = (int)(items >= full ? (long long)ctx->sms * rq::kCtasPerSm
+                                         : std::min<long long>(ctx->sms, (items + 31) / 32));
     std::vector<int32_t> cols;
     std::vector<double> wts;
     std::vector<int> tpar;
@@ -1285,6 +1290,10 @@ rq_status rq_hessian(rq_ctx *ctx, const double *gates, double *f, double *egrad,
     const int g = ctx->g, P = ctx->P, B = ctx->B;
     const int log2M = ctx->structure == 1 ? 3 : 4, M = 1 << log2M;
     const long long tile = ctx->n_store * B;
+    // CTAs of the hole kernels (one thread per item and member, grid M high):
+    // one block of items per CTA at most, so small problems launch few CTAs
+    const int nh = (int)std::min<long long>((long long)ctx->sms * rq::kCtasPerSm,
+                                            std::max<long long>(1, (ctx->n_store / 4 * B + rq::kThreads - 1) / rq::kThreads));
     // temporaries: adjoint checkpoints, two member arrays, partials, block accumulators
     long long tmp_bytes = 0;
     double2 *lamck = nullptr, *arr0 = nullptr, *arr1 = nullptr;
@@ -1300,7 +1309,7 @@ rq_status rq_hessian(rq_ctx *ctx, const double *gates, double *f, double *egrad,
     rq_status st = dev_alloc(ctx, &lamck, tile * g, tmp_bytes);
     if (st == RQ_OK) st = dev_alloc(ctx, &arr0, tile * M, tmp_bytes);
     if (st == RQ_OK) st = dev_alloc(ctx, &arr1, tile * M, tmp_bytes);
-    if (st == RQ_OK) st = dev_alloc(ctx, &hpart, (long long)g * M * ctx->ncta * rq::kEnvDoubles, tmp_bytes);
+    if (st == RQ_OK) st = dev_alloc(ctx, &hpart, (long long)g * M * nh * rq::kEnvDoubles, tmp_bytes);
     if (st == RQ_OK) st = dev_alloc(ctx, &hacc, (long long)g * g * M * rq::kEnvDoubles, tmp_bytes);
     if (st != RQ_OK) {
         cleanup();
@@ -1372,14 +1381,14 @@ rq_status rq_hessian(rq_ctx *ctx, const double *gates, double *f, double *egrad,
             const GateGeom &geo = ctx->geo[l];
             const long long items_l = (geo.mode == rq::kParity2 ? ctx->n_store / 2 : ctx->n_store / 4) * B;
             rq::launch_hole_apply(ctx->d_psi + l * tile, arr0, geo, ctx->log2B, log2M, ctx->structure, par, items_l,
-                                  ctx->ncta, s);
+                                  nh, s);
             RQH_LAUNCHED();
             double2 *cur = arr0, *nxt = arr1;
             for (int lp = l + 1; lp < g; ++lp) {
                 const GateGeom &gp = ctx->geo[lp];
                 const long long items = (gp.mode == rq::kParity2 ? ctx->n_store / 2 : ctx->n_store / 4) * B;
-                rq::launch_array_env(lamck + lp * tile, cur, gp, ctx->log2B, log2M, par, items, ctx->ncta,
-                                     hpart + (long long)lp * M * ctx->ncta * rq::kEnvDoubles, s);
+                rq::launch_array_env(lamck + lp * tile, cur, gp, ctx->log2B, log2M, par, items, nh,
+                                     hpart + (long long)lp * M * nh * rq::kEnvDoubles, s);
                 RQH_LAUNCHED();
                 if (lp + 1 < g) {
                     rq::FwdArgs a{};
@@ -1396,7 +1405,7 @@ rq_status rq_hessian(rq_ctx *ctx, const double *gates, double *f, double *egrad,
                     std::swap(cur, nxt);
                 }
             }
-            rq::launch_reduce_rows(hpart + (long long)(l + 1) * M * ctx->ncta * rq::kEnvDoubles, ctx->ncta,
+            rq::launch_reduce_rows(hpart + (long long)(l + 1) * M * nh * rq::kEnvDoubles, nh,
                                    (long long)(g - 1 - l) * M, hacc + ((long long)l * g + l + 1) * M * rq::kEnvDoubles, s);
             RQH_LAUNCHED();
         }
