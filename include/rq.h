@@ -150,8 +150,13 @@ rq_status rq_destroy(rq_ctx *ctx);
  * evaluation") is realised by per-sector blocks: H conserves the spin-resolved
  * particle numbers, so U is block diagonal over (N_up, N_down) sectors; each
  * block is built on the device by a Chebyshev expansion of exp(-iHt) with the
- * sparse H.  Resets the column range to all 2^n columns.  Errors: RQ_EINVAL
- * for an invalid circuit/target, RQ_ENOMEM if the workspace does not fit. */
+ * sparse H.  Resets the column range to all 2^n columns, the translation
+ * and the checkpointing request; the tile request, arithmetic, output space,
+ * graphs, checks and first-layer settings of the context persist.  A context
+ * may be set up again for another problem at any time (the previous problem's
+ * device memory is released first).  Errors: RQ_EINVAL for an invalid
+ * circuit/target, RQ_ENOMEM if the target or the workspace does not fit; the
+ * context then holds no problem (RQ_ESTATE until the next set-up). */
 rq_status rq_setup_target(rq_ctx *ctx, const rq_target *target, const rq_circuit *circuit);
 
 /* Restrict the basis sum to columns j in [col_begin, col_end) (shards of
