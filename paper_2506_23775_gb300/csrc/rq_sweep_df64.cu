@@ -107,7 +107,47 @@ __device__ __forceinline__ double2 to_double(const CAcc &c) {
     return make_double2((double)c.re.h + (double)c.re.l, (double)c.im.h + (double)c.im.l);
 }
 
+// df64 sum a + b, renormalised (two-sum of the high parts, low parts and the
+// rounding error added, one more two-sum)
+__device__ __forceinline__ float2 df_add(float ah, float al, float bh, float bl) {
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(al, bl));
+    float h, l;
+    two_sum(s, e, h, l);
+    return make_float2(h, l);
+}
 
+// General gates in the forward sweep use the three-product form (as the FP64
+// kernels do): for m = a + ib and x = u + iv, m x = (k - b (u + v)) +
+// i (k + a (v - u)) with k = u (a + b).  In df64 a product term costs as much
+// as before but the sums u + v, v - u are formed once per amplitude and serve
+// all four rows, and a + b once per gate entry.
+struct MatDf3 {
+    float2 s[16], a[16], nb[16];  // a + b, a, -b
+};
+
+__device__ __forceinline__ void tabulate_df3(MatDf3 &m, const float4 *g, int e) {
+    const float4 x = g[e];
+    m.s[e] = df_add(x.x, x.y, x.z, x.w);
+    m.a[e] = make_float2(x.x, x.y);
+    m.nb[e] = make_float2(-x.z, -x.w);
+}
+
+// x = u + iv with S = u + v, D = v - u
+struct AmpDf3 {
+    float uh, ul;
+    float2 S, D;
+};
+
+__device__ __forceinline__ AmpDf3 amp_df3(const float4 x) {
+    AmpDf3 r;
+    r.uh = x.x;
+    r.ul = x.y;
+    r.S = df_add(x.x, x.y, x.z, x.w);
+    r.D = df_add(x.z, x.w, -x.x, -x.y);
+    return r;
+}
 
 __device__ __forceinline__ void offsets2(long long r, long long b, int p, int qfirst, int parity, int log2B,
                                          long long (&off)[2], int &i0, int &i1) {
@@ -166,11 +206,19 @@ template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1) k_fwd_df(const FwdArgs a) {
     __shared__ float4 sg[16];
     __shared__ float4 sx[kMaxDirs][16];
+    __shared__ MatDf3 sg3;
+    __shared__ MatDf3 sx3[kMaxDirs];
     const float4 *gate = reinterpret_cast<const float4 *>(a.gate);
     const float4 *dirs = reinterpret_cast<const float4 *>(a.dirs);
-    if (threadIdx.x < 16) sg[threadIdx.x] = gate[threadIdx.x];
-    if (threadIdx.x < 16 * a.kdirs)
-        sx[threadIdx.x >> 4][threadIdx.x & 15] = dirs[(threadIdx.x >> 4) * a.xdir_stride + (threadIdx.x & 15)];
+    if (MODE == kGeneral) {
+        if (threadIdx.x < 16) tabulate_df3(sg3, gate, threadIdx.x);
+        if (threadIdx.x < 16 * a.kdirs)
+            tabulate_df3(sx3[threadIdx.x >> 4], dirs + (threadIdx.x >> 4) * a.xdir_stride, threadIdx.x & 15);
+    } else {
+        if (threadIdx.x < 16) sg[threadIdx.x] = gate[threadIdx.x];
+        if (threadIdx.x < 16 * a.kdirs)
+            sx[threadIdx.x >> 4][threadIdx.x & 15] = dirs[(threadIdx.x >> 4) * a.xdir_stride + (threadIdx.x & 15)];
+    }
     __syncthreads();
     const float4 *psi_in = reinterpret_cast<const float4 *>(a.psi_in);
     float4 *psi_out = reinterpret_cast<float4 *>(a.psi_out);
@@ -180,7 +228,53 @@ __global__ void __launch_bounds__(kThreads, 1) k_fwd_df(const FwdArgs a) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long it = first_item(); it < a.n_items; it += stride) {
         const long long b = it & Bm, r = it >> a.log2B;
-        if (MODE == kGeneral || MODE == kParity4) {
+        if constexpr (MODE == kGeneral) {
+            long long off[4];
+            if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
+            AmpDf3 x[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) x[c] = amp_df3(__ldg(&psi_in[off[c]]));
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                Acc k;
+                acc_set(k, x[0].uh, x[0].ul, sg3.s[i * 4].x, sg3.s[i * 4].y);
+#pragma unroll
+                for (int c = 1; c < 4; ++c) acc_mac(k, x[c].uh, x[c].ul, sg3.s[i * 4 + c].x, sg3.s[i * 4 + c].y);
+                CAcc q{k, k};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    acc_mac(q.re, sg3.nb[i * 4 + c].x, sg3.nb[i * 4 + c].y, x[c].S.x, x[c].S.y);
+                    acc_mac(q.im, sg3.a[i * 4 + c].x, sg3.a[i * 4 + c].y, x[c].D.x, x[c].D.y);
+                }
+                psi_out[off[i]] = fin(q);
+            }
+            for (int d = 0; d < a.kdirs; ++d) {
+                const float4 *din = dpsi_in + d * a.dir_stride;
+                float4 *dout = dpsi_out + d * a.dir_stride;
+                AmpDf3 t[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) t[c] = amp_df3(__ldg(&din[off[c]]));
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {  // G psi' + X psi
+                    Acc k;
+                    acc_set(k, t[0].uh, t[0].ul, sg3.s[i * 4].x, sg3.s[i * 4].y);
+#pragma unroll
+                    for (int c = 1; c < 4; ++c) acc_mac(k, t[c].uh, t[c].ul, sg3.s[i * 4 + c].x, sg3.s[i * 4 + c].y);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        acc_mac(k, x[c].uh, x[c].ul, sx3[d].s[i * 4 + c].x, sx3[d].s[i * 4 + c].y);
+                    CAcc q{k, k};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        acc_mac(q.re, sg3.nb[i * 4 + c].x, sg3.nb[i * 4 + c].y, t[c].S.x, t[c].S.y);
+                        acc_mac(q.re, sx3[d].nb[i * 4 + c].x, sx3[d].nb[i * 4 + c].y, x[c].S.x, x[c].S.y);
+                        acc_mac(q.im, sg3.a[i * 4 + c].x, sg3.a[i * 4 + c].y, t[c].D.x, t[c].D.y);
+                        acc_mac(q.im, sx3[d].a[i * 4 + c].x, sx3[d].a[i * 4 + c].y, x[c].D.x, x[c].D.y);
+                    }
+                    dout[off[i]] = fin(q);
+                }
+            }
+        } else if constexpr (MODE == kParity4) {
             long long off[4];
             if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
             float4 p[4];
