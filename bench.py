@@ -566,6 +566,12 @@ def run_ours(args):
                                 "sample": f"{cores} basis columns of the (4,4) sector, one per spawned process, "
                                           "numpy oracle (paper's matrix-free algorithm), general gates; "
                                           "evals/s = columns / 65536 / slowest process time"}
+    # the paper's own CPU figures, for context only: its timings are plots
+    # without numbers in the text
+    line["paper_cpu_context"] = {"hardware": "2x Intel Xeon Platinum 8480+, up to 112 threads (one node); "
+                                             "MPI up to 448 cores",
+                                 "numbers": "gradient time per summand and thread / MPI scaling are given as plots "
+                                            "only; no throughput figure for f, the gradient or HVPs in the text"}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
