@@ -67,6 +67,9 @@ def test_graph_replay_is_bitwise_equal(rq, name, structure):
         c.set_gradient_space(1)
         c.set_tile(0, 1)
     _same(_all(graphed, prob.gates, X), _all(direct, prob.gates, X))
+    for c in (direct, graphed):
+        c.set_first_layer(False)
+    _same(_all(graphed, prob.gates, X), _all(direct, prob.gates, X))
     # more directions than the buffers held: reallocation, then recapture
     X7 = w.random_directions(prob.n_params, 7, 6)
     a, b = graphed.hvp(prob.gates, X7), direct.hvp(prob.gates, X7)
