@@ -230,12 +230,16 @@ rq_status rq_set_first_layer(rq_ctx *ctx, int enable);
 rq_status rq_set_checks(rq_ctx *ctx, int enable);
 
 /* CUDA graphs for the host-memory calls (rq_cost, rq_grad, rq_hvp and the
- * evaluations inside rq_tr_step): with enable = 1 (default) the kernel
- * sequence of an evaluation is captured once per (k, kind) and replayed as one
- * graph launch until the context's configuration changes (columns, tile,
- * arithmetic, output space, translation, checkpointing, profiling), which
- * removes the per-kernel launch cost of small problems.  Results are bitwise
- * those of direct launches.  enable = 0 launches kernels directly. */
+ * evaluations inside rq_tr_step; a launch mechanism, no counterpart in the
+ * paper): with enable = 1 (default) the kernel sequence of an evaluation is
+ * captured once per (k, kind) and replayed as one graph launch until the
+ * context's configuration changes what the kernels are given (tile layout,
+ * arithmetic, output space, translation, checkpointing, first-layer support,
+ * profiling; a new column range of the same layout keeps the graphs), which
+ * removes the host's per-kernel launch cost.  Results are bitwise those of
+ * direct launches.  enable = 0 launches kernels directly.  A stream that
+ * cannot be captured (the legacy default stream) falls back to direct
+ * launches. */
 rq_status rq_set_graphs(rq_ctx *ctx, int enable);
 
 /* Checkpointing of the forward pass (memory vs recomputation).  interval 1
