@@ -46,9 +46,12 @@
 // as three sums, K1 = sum u (p - q), K2 = sum p (v - u), K3 = sum q (u + v),
 // with Re = K1 + K3 and Im = K1 + K2 formed once per thread before the block
 // reduction.  GB300's FP64 pipe is the bound of these kernels, and this cuts
-// the FP64 instructions of a general-gate item by 12.5-17 %; the parity-gate
-// paths touch two entries per row, where the per-amplitude sums cost as much
-// as they save, so they keep the four-product form.
+// the FP64 instructions of a general-gate item by 12.5-17 %.  Parity gates
+// touch two entries per row, where the per-amplitude sums cost as much as
+// they save, so their backward steps keep the four-product form; their
+// forward step with tangents uses three products, the state's sums serving
+// both its own rows and the tangents' (88 instead of 96 per item and
+// direction).
 #include "rq_items.cuh"
 
 namespace rq {
@@ -149,6 +152,46 @@ __device__ __forceinline__ void matvec3_pair(const Mat3 &m, const Amp3 (&x)[4], 
             re = fma(n.nb[i * 4 + c], w[c].S, re);
             im = fma(n.a[i * 4 + c], w[c].D, im);
         }
+        y[i] = make_double2(re, im);
+    }
+}
+
+// Columns of row i of a parity gate (Eq. paritygatematrix): {0, 3} for rows 0
+// and 3, {1, 2} for rows 1 and 2.
+__device__ __forceinline__ int pcol(int i, int u) {
+    return (i == 0 || i == 3) ? (u == 0 ? 0 : 3) : (u == 0 ? 1 : 2);
+}
+
+// matvec3 for a parity gate: two terms per row.
+__device__ __forceinline__ void matvec3_blocks(const Mat3 &m, const Amp3 (&x)[4], double2 (&y)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int c0 = pcol(i, 0), c1 = pcol(i, 1);
+        const double k = fma(x[c1].u, m.s[i * 4 + c1], x[c0].u * m.s[i * 4 + c0]);
+        const double re = fma(m.nb[i * 4 + c1], x[c1].S, fma(m.nb[i * 4 + c0], x[c0].S, k));
+        const double im = fma(m.a[i * 4 + c1], x[c1].D, fma(m.a[i * 4 + c0], x[c0].D, k));
+        y[i] = make_double2(re, im);
+    }
+}
+
+// matvec3_pair for parity gates: y = M x + N w, two terms per row each.
+__device__ __forceinline__ void matvec3_pair_blocks(const Mat3 &m, const Amp3 (&x)[4], const Mat3 &n,
+                                                    const Amp3 (&w)[4], double2 (&y)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int c0 = pcol(i, 0), c1 = pcol(i, 1);
+        double k = x[c0].u * m.s[i * 4 + c0];
+        k = fma(x[c1].u, m.s[i * 4 + c1], k);
+        k = fma(w[c0].u, n.s[i * 4 + c0], k);
+        k = fma(w[c1].u, n.s[i * 4 + c1], k);
+        double re = fma(m.nb[i * 4 + c0], x[c0].S, k);
+        re = fma(m.nb[i * 4 + c1], x[c1].S, re);
+        re = fma(n.nb[i * 4 + c0], w[c0].S, re);
+        re = fma(n.nb[i * 4 + c1], w[c1].S, re);
+        double im = fma(m.a[i * 4 + c0], x[c0].D, k);
+        im = fma(m.a[i * 4 + c1], x[c1].D, im);
+        im = fma(n.a[i * 4 + c0], w[c0].D, im);
+        im = fma(n.a[i * 4 + c1], w[c1].D, im);
         y[i] = make_double2(re, im);
     }
 }
@@ -262,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fwd(const FwdArgs a) {
     __shared__ double2 sx[kMaxDirs][16];
     __shared__ Mat3 sg3;
     __shared__ Mat3 sx3[kMaxDirs];
-    if (MODE == kGeneral) {
+    if (MODE == kGeneral || MODE == kParity4) {
         if (threadIdx.x < 16) tabulate3(sg3, a.gate, threadIdx.x, 0);
         if (threadIdx.x < 16 * a.kdirs)
             tabulate3(sx3[threadIdx.x >> 4], a.dirs + (threadIdx.x >> 4) * a.xdir_stride, threadIdx.x & 15, 0);
@@ -297,36 +340,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_fwd(const FwdArgs a) {
                 for (int c = 0; c < 4; ++c) dout[off[c]] = q[c];
             }
         } else if constexpr (MODE == kParity4) {
+            // the three-product form on each row's two entries (block {0, 3}
+            // or {1, 2}); the tangent shares the state's sums
             long long off[4];
             if (!item_offsets4(a.geo, a.cols, r, b, a.log2B, off)) continue;
-            double2 p[4];
+            Amp3 x[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) p[c] = __ldg(&a.psi_in[off[c]]);
+            for (int c = 0; c < 4; ++c) x[c] = amp3(__ldg(&a.psi_in[off[c]]));
             double2 q[4];
-            q[0] = zero2(); cmac(q[0], sg[0], p[0]); cmac(q[0], sg[3], p[3]);
-            q[3] = zero2(); cmac(q[3], sg[12], p[0]); cmac(q[3], sg[15], p[3]);
-            q[1] = zero2(); cmac(q[1], sg[5], p[1]); cmac(q[1], sg[6], p[2]);
-            q[2] = zero2(); cmac(q[2], sg[9], p[1]); cmac(q[2], sg[10], p[2]);
+            matvec3_blocks(sg3, x, q);
 #pragma unroll
             for (int c = 0; c < 4; ++c) a.psi_out[off[c]] = q[c];
             for (int d = 0; d < a.kdirs; ++d) {
                 const double2 *din = a.dpsi_in + d * a.dir_stride;
                 double2 *dout = a.dpsi_out + d * a.dir_stride;
-                double2 t[4];
+                Amp3 t[4];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) t[c] = __ldg(&din[off[c]]);
-                const int E0[2] = {0, 3}, O0[2] = {1, 2};
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int i = E0[u];
-                    q[i] = zero2();
-                    cmac(q[i], sg[i * 4 + 0], t[0]); cmac(q[i], sg[i * 4 + 3], t[3]);
-                    cmac(q[i], sx[d][i * 4 + 0], p[0]); cmac(q[i], sx[d][i * 4 + 3], p[3]);
-                    const int o = O0[u];
-                    q[o] = zero2();
-                    cmac(q[o], sg[o * 4 + 1], t[1]); cmac(q[o], sg[o * 4 + 2], t[2]);
-                    cmac(q[o], sx[d][o * 4 + 1], p[1]); cmac(q[o], sx[d][o * 4 + 2], p[2]);
-                }
+                for (int c = 0; c < 4; ++c) t[c] = amp3(__ldg(&din[off[c]]));
+                matvec3_pair_blocks(sg3, t, sx3[d], x, q);  // G psi' + X psi
 #pragma unroll
                 for (int c = 0; c < 4; ++c) dout[off[c]] = q[c];
             }
