@@ -34,3 +34,22 @@ def target_for(prob):
 def oracle_eval(prob, cols, Xraw=None, gates=None, chunk=16):
     from oracle import statevector as sv
     return sv.cost_grad_hvp(prob, target_for(prob), list(cols), Xraw, gates=gates, chunk=chunk)
+
+
+def load_golden(fname):
+    """A file of oracle-written values under tests/golden/ (make_golden.py),
+    with every {"shape", "re", "im"} entry turned into a complex array."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", fname)) as fh:
+        data = json.load(fh)
+
+    def conv(d):
+        if isinstance(d, dict):
+            if set(d) == {"shape", "re", "im"}:
+                return (np.array(d["re"]) + 1j * np.array(d["im"])).reshape(d["shape"])
+            return {k: conv(v) for k, v in d.items()}
+        if isinstance(d, list):
+            return [conv(v) for v in d]
+        return d
+    return conv(data)

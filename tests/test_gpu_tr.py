@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import workloads as w
-from tests._helpers import target_for
+from tests._helpers import load_golden, target_for
 
 pytestmark = pytest.mark.gpu
 
@@ -79,3 +79,48 @@ def test_thirty_iterations_tied_parity_twelve_qubits(rq):
     for p in range(prob.n_params):
         np.testing.assert_allclose(G[p].conj().T @ G[p], np.eye(4), atol=1e-12)
         assert np.all(G[p][~mask] == 0)
+
+
+def _follow(rq, ctx, prob, gold, r0, rmax, what):
+    """Device trust-region steps against the oracle's trajectory step by step:
+    identical acceptance, inner iterations and tCG exit; f to 1e-12, rho to
+    1e-6, the radius after the step to 1e-12 and the gates (where stored) to
+    1e-10."""
+    st = rq.tr_state(radius=r0, max_radius=rmax)
+    G = prob.gates.copy()
+    for rec in gold:
+        G = ctx.tr_step(G, st)
+        it = (what, rec["step"])
+        assert st.n_inner == rec["n_inner"] and st.tcg_exit == rec["tcg_exit"], (it, st.n_inner, st.tcg_exit)
+        assert bool(st.accepted) == rec["accepted"], it
+        assert abs(st.f - rec["f"]) <= 1e-12 * abs(rec["f"]), (it, st.f, rec["f"])
+        assert abs(st.f_new - rec["f_new"]) <= 1e-11 * abs(rec["f_new"]), (it, st.f_new, rec["f_new"])
+        assert abs(st.rho - rec["rho"]) <= 1e-6 * max(1.0, abs(rec["rho"])), (it, st.rho, rec["rho"])
+        assert st.radius == pytest.approx(rec["radius"], rel=1e-12), (it, st.radius, rec["radius"])
+        if "gates" in rec:
+            assert np.abs(G - rec["gates"]).max() <= 1e-10, (it, np.abs(G - rec["gates"]).max())
+    return G, st
+
+
+def test_tied_parity_twelve_qubits_trajectory_matches_oracle(rq):
+    """Three iterations over all 4096 columns of the tied parity n = 12
+    workload against the oracle's trust region (tests/golden/make_golden.py)."""
+    gold = load_golden("tr12_trajectory.json")
+    prob = w.config_problem("tied12")
+    ctx = rq.Context(0).setup_problem(prob)
+    _follow(rq, ctx, prob, gold["steps"], gold["radius0"], gold["max_radius"], "tied12")
+
+
+@pytest.mark.parametrize("key", ["long", "shrink"])
+def test_n8_trajectory_matches_oracle(rq, key):
+    """Thirty iterations (radius growth, boundary and interior tCG exits), and
+    six from a far start with an oversized radius (rejections, shrinks), at
+    n = 8 against the oracle's trajectories; the final f to 1e-9."""
+    gold = load_golden("tr8_trajectory.json")[key]
+    prob = w.make_problem(gold["L"], gold["depth"], gold["t"], seed=gold["seed"], sigma=gold["sigma"])
+    ctx = rq.Context(0).setup_problem(prob)
+    G, st = _follow(rq, ctx, prob, gold["steps"], gold["radius0"], gold["max_radius"], key)
+    last = gold["steps"][-1]
+    f_last = last["f_new"] if last["accepted"] else last["f"]
+    f_dev = st.f_new if st.accepted else st.f
+    assert abs(f_dev - f_last) <= 1e-9 * abs(f_last)
