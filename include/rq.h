@@ -225,8 +225,8 @@ rq_status rq_set_first_layer(rq_ctx *ctx, int enable);
  * ||G^H G - I||_F <= 1e-10 (the gates are points of U(4), Sec. "Riemannian
  * optimization"), and for parity gates (Eq. paritygatematrix) no entry above
  * 1e-10 outside the parity pattern.  A failed check returns RQ_EINVAL with the
- * gate index and the deviation in rq_last_error, before any launch.  The
- * batch and rq_cost_static calls do not check. */
+ * gate index and the deviation in rq_last_error, before any launch
+ * (rq_cost_static included).  The batch calls do not check. */
 rq_status rq_set_checks(rq_ctx *ctx, int enable);
 
 /* CUDA graphs for the host-memory calls (rq_cost, rq_grad, rq_hvp and the
@@ -340,7 +340,12 @@ rq_status rq_get_info(const rq_ctx *ctx, rq_info_t *info);
  * caches it; make that first call before any stream capture.  Every call,
  * from any context on the device, shares the array and finds the previous
  * call's contents there (each call clears what must start at zero); calls
- * whose GPU work overlaps race on it and give wrong results. */
+ * whose GPU work overlaps race on it and give wrong results.  The cached
+ * address does not survive a cudaDeviceReset: do not keep using the library
+ * on a device after resetting it.  The sweep is always FP64 over every column
+ * of the range (rq_set_arithmetic and rq_set_translation do not apply; the
+ * full sum equals the translation-weighted one), and gates are validated as
+ * in rq_cost when rq_set_checks is on. */
 #define RQ_STATIC_SCRATCH_BYTES (16u << 20)
 rq_status rq_cost_static(rq_ctx *ctx, const double *gates, double *f);
 

@@ -16,6 +16,13 @@
 // the contents of the last call; each call clears what must start at zero.
 // Calls whose GPU work overlaps (several host threads, or several streams)
 // race on the array and give wrong results: serialise them.
+//
+// The sweep here is always the FP64 one over the context's whole column range
+// (rq_set_arithmetic and rq_set_translation do not apply: the sum over every
+// column of the range equals the weighted sum over orbit representatives).
+// The array's device address is looked up once per device and kept for the
+// life of the process, so the library must not outlive a cudaDeviceReset of a
+// device it has used.
 #include "rq_internal.h"
 
 #include <algorithm>
@@ -82,6 +89,11 @@ extern "C" rq_status rq_cost_static(rq_ctx *ctx, const double *gates, double *f)
     const rq::CtxView v = rq::ctx_view(ctx);
     if (!v.ready) return err(ctx, RQ_ESTATE, "no target set up (call rq_setup_target first)");
     if (!gates || !f) return err(ctx, RQ_EINVAL, "gates or f is NULL");
+    // the same host-side validation as rq_cost when rq_set_checks is on
+    {
+        const rq_status cs = rq::check_gates(ctx, gates);
+        if (cs != RQ_OK) return cs;
+    }
     if (v.device < 0 || v.device >= kMaxDevices) return err(ctx, RQ_EINVAL, "device ordinal too large");
 
     int prev_dev = 0;
