@@ -46,13 +46,36 @@ def sum_in_rank_order(stack: np.ndarray) -> np.ndarray:
     return out
 
 
+def exchange(part, group=None) -> np.ndarray:
+    """All-gather one packed partial per rank and return their rank-order sum.
+
+    ``part`` is a 1-D float64 tensor of the same length on every rank: on the
+    current CUDA device for NCCL (the gather stays on the devices; only the
+    gathered rows come to the host for the sum), on the CPU for gloo.  The sum
+    runs on the host in rank order, so every rank gets the same bits.
+    """
+    import torch
+    import torch.distributed as dist
+
+    world = dist.get_world_size(group)
+    part = part.contiguous()
+    if dist.get_backend(group) == "nccl":
+        out = torch.empty((world,) + tuple(part.shape), dtype=part.dtype, device=part.device)
+        dist.all_gather_into_tensor(out, part, group=group)
+        return sum_in_rank_order(out.cpu().numpy())
+    part = part.cpu()          # gloo gathers host tensors, one per rank
+    bufs = [torch.empty_like(part) for _ in range(world)]
+    dist.all_gather(bufs, part, group=group)
+    return sum_in_rank_order(np.stack([b.numpy() for b in bufs]))
+
+
 def sharded_eval(evaluate: Callable[[int, int], Tuple[float, np.ndarray, Optional[np.ndarray]]],
                  n_cols: int, n_params: int, k: int, group=None):
     """Evaluate this rank's shard with ``evaluate(c0, c1)`` and return the total.
 
     ``evaluate`` returns ``(f, rgrad, hvps)`` for the columns ``[c0, c1)`` (for
     example a device context restricted with ``rq_set_columns``).  The
-    exchange is one ``all_gather`` of the packed partials over
+    exchange is one all-gather of the packed partials over
     ``torch.distributed`` (gloo or NCCL); the sum is in rank order.
     """
     import torch
@@ -61,14 +84,45 @@ def sharded_eval(evaluate: Callable[[int, int], Tuple[float, np.ndarray, Optiona
     world = dist.get_world_size(group)
     rank = dist.get_rank(group)
     c0, c1 = column_shard(n_cols, rank, world)
-    part = pack(*evaluate(c0, c1))
-    backend = dist.get_backend(group)
-    dev = torch.device("cuda", torch.cuda.current_device()) if backend == "nccl" else torch.device("cpu")
-    t = torch.from_numpy(part).to(dev)
-    bufs = [torch.empty_like(t) for _ in range(world)]
-    dist.all_gather(bufs, t, group=group)
-    stack = np.stack([b.cpu().numpy() for b in bufs])
-    return unpack(sum_in_rank_order(stack), n_params, k)
+    part = torch.from_numpy(pack(*evaluate(c0, c1)))
+    if dist.get_backend(group) == "nccl":
+        part = part.to(torch.device("cuda", torch.cuda.current_device()))
+    return unpack(exchange(part, group), n_params, k)
+
+
+class DeviceShard:
+    """Device-resident partials of one rank for the device-pointer entry points.
+
+    ``buf`` is one float64 CUDA tensor laid out as ``[f, pad, rgrad, hvps]``
+    (complex outputs 16-byte aligned, as the library requires), so that
+    ``rq_hvp_dev`` writes this rank's partial straight into the buffer that
+    the all-gather sends; ``total()`` exchanges it and returns
+    ``(f, rgrad, hvps)`` summed in rank order.
+    """
+
+    def __init__(self, ctx, n_params: int, k: int, device):
+        import torch
+        self.ctx, self.P, self.k = ctx, n_params, k
+        self.buf = torch.zeros(2 + 32 * n_params * (1 + k), dtype=torch.float64, device=device)
+        base = self.buf.data_ptr()
+        self.f_ptr = base
+        self.g_ptr = base + 16
+        self.h_ptr = base + 16 + 8 * 32 * n_params
+
+    def evaluate(self, gates_ptr: int, dirs_ptr: int):
+        """This rank's partial over the context's column range (stream-ordered)."""
+        self.ctx.hvp_dev(gates_ptr, dirs_ptr, self.k, self.f_ptr, self.g_ptr, self.h_ptr)
+
+    def total(self, stream=None, group=None):
+        import torch
+        if stream is not None:
+            torch.cuda.current_stream().wait_stream(stream)
+        v = exchange(self.buf, group)
+        gsz = 32 * self.P
+        f = float(v[0])
+        rg = v[2:2 + gsz].copy().view(np.complex128).reshape(self.P, 4, 4)
+        hv = v[2 + gsz:2 + gsz * (1 + self.k)].copy().view(np.complex128).reshape(self.k, self.P, 4, 4)
+        return f, rg, hv
 
 
 def context_evaluator(ctx, gates, dirs):

@@ -76,6 +76,25 @@ def test_two_rank_gloo_sum_matches_unsharded(tmp_path):
     np.testing.assert_allclose(r["hv"], hv, atol=1e-13 * np.abs(hv).max())
 
 
+def _exchange_worker(rank, world, port, out_path):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    part = torch.arange(7, dtype=torch.float64) * (rank + 1) + 0.1 * rank
+    total = shard.exchange(part)
+    if rank == 0:
+        np.save(out_path, total)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_exchange_sums_partials_in_rank_order(tmp_path):
+    out = str(tmp_path / "x.npy")
+    mp.spawn(_exchange_worker, args=(3, _free_port(), out), nprocs=3, join=True)
+    rows = [np.arange(7, dtype=np.float64) * (r + 1) + 0.1 * r for r in range(3)]
+    assert np.array_equal(np.load(out), (rows[0] + rows[1]) + rows[2])
+
+
 def _failing_worker(rank, world, port, out_path):
     import datetime
     os.environ["MASTER_ADDR"] = "127.0.0.1"
