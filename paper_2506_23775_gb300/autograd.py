@@ -11,7 +11,8 @@ Gradients follow PyTorch's convention for a real loss of complex inputs,
 ``dL/dx + i dL/dy``, which is the paper's gradient convention (Eq. def_grad).
 They are *Euclidean*: the cost is extended to all complex matrices, so
 ``gates.grad`` is ``gbar`` of Eq. grad_proj before the tangent projection
-(a Riemannian optimiser projects it, e.g. with :func:`riemannian_gradient`).
+(a Riemannian optimiser projects it; the library's own Riemannian outputs
+are those of ``rq_set_gradient_space(ctx, RQ_SPACE_RIEMANNIAN)``).
 For parity-structured circuits the cost is restricted to the pattern of
 Eq. paritygatematrix, so gradients and HVPs are masked to it.
 
@@ -102,9 +103,3 @@ class _Cost(torch.autograd.Function):
 def circuit_cost(gates: torch.Tensor, ctx) -> torch.Tensor:
     """Differentiable ``f(G)`` over the context's column range (0-dim float64)."""
     return _Cost.apply(gates, ctx)
-
-
-def riemannian_gradient(gates: torch.Tensor, egrad: torch.Tensor) -> torch.Tensor:
-    """``P_G(gbar) = G skew(G^dagger gbar)`` (Eq. proj_tangent) in torch."""
-    m = gates.conj().transpose(-1, -2) @ egrad
-    return gates @ (0.5 * (m - m.conj().transpose(-1, -2)))
