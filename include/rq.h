@@ -254,6 +254,28 @@ rq_status rq_set_graphs(rq_ctx *ctx, int enable);
  * tile size may grow); rq_hessian needs an effective interval of 1. */
 rq_status rq_set_checkpointing(rq_ctx *ctx, int interval);
 
+/* Window fusion of the forward pass (Sec. "Brick wall circuit layout": the
+ * gates of a layer act on disjoint qubits and commute).  max_window_qubits 0
+ * (default): every gate is one pass over the tile, in circuit order.  3..6:
+ * after the leading run of disjoint gates, consecutive gates -- reordered
+ * only past gates on disjoint qubits, with which they commute -- whose
+ * qubits fit in a window of that many stored qubits form one pass: a CTA
+ * holds [2^q amplitudes x 32 columns] of the state (and of each tangent) in
+ * shared memory, applies the pass's gates (at most 16) there, and writes to
+ * HBM only the checkpoints the backward pass needs (every state of a
+ * gradient or HVP evaluation; only the pass's output for a cost).  The
+ * backward pass runs the same order in reverse.  Parity gates on the implied
+ * qubit 0 are not fused.  Fusion applies when the checkpoint interval is 1
+ * and tiles have at least 32 columns; otherwise the unfused schedule runs.
+ * Results equal the unfused ones up to the order of floating-point sums.
+ * Returns RQ_EINVAL for a window outside {0} U [3, 6].  The setting is kept
+ * across rq_setup_target.
+ *
+ * rq_fusion_info: number of passes of the current plan, gates inside
+ * multi-gate passes, and the largest pass (any output may be NULL). */
+rq_status rq_set_fusion(rq_ctx *ctx, int max_window_qubits);
+rq_status rq_fusion_info(const rq_ctx *ctx, int *n_passes, int *fused_gates, int *max_pass_gates);
+
 /* Arithmetic of the sweep kernels (forward, adjoint, environments).
  * RQ_ARITH_FP64 (default): IEEE binary64 on the FP64 pipe.  RQ_ARITH_DF64:
  * every amplitude and gate entry is kept as an unevaluated sum of two floats
@@ -374,6 +396,15 @@ rq_status rq_batch_set_tile(rq_batch *b, int columns_per_tile);
 rq_status rq_batch_hvp(rq_batch *b, const double *gates, const double *dirs, int k, int plain, double *f,
                        double *rgrad, double *hvps);
 rq_status rq_batch_info(const rq_batch *b, int *n_problems, int *columns_per_tile, double *tune_ms);
+/* Gates per forward pass of every problem of the batch (rq_set_fusion).
+ * max_window_qubits -1 (default): autotuned at the first evaluation after the
+ * tile size, by timing the captured cost-only batch evaluation with fusion
+ * off and with windows of 4, 5 and 6 stored qubits and keeping the fastest;
+ * 0: off; 3..6: that window for every problem.  rq_batch_fusion_info: the
+ * window in use and the autotuner's timings (ms for windows 0, 4, 5, 6; -1
+ * where not timed). */
+rq_status rq_batch_set_fusion(rq_batch *b, int max_window_qubits);
+rq_status rq_batch_fusion_info(const rq_batch *b, int *window, double *tune_ms);
 const char *rq_batch_last_error(const rq_batch *b);
 
 /* Per-kernel timing of one context (benchmarking and roofline accounting).

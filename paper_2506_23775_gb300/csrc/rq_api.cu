@@ -107,6 +107,15 @@ struct rq_ctx {
     long long version = 0, graph_clock = 0;
     int checks = 0;  // validate the gates of every call (unitarity, parity pattern)
     bool first_layer = true;  // FP64 sweeps of the leading disjoint gates visit only nonzero items
+    // window fusion of the forward pass (rq_set_fusion): execution order of
+    // the gates (a reordering of commuting disjoint gates) and its passes
+    int fuse_q = 0;  // largest window in stored bits; 0: off (every gate its own pass, original order)
+    struct PassPlan {
+        int pos, m;        // first position in `order`, number of gates
+        long long wmask;   // stored bits of the window
+    };
+    std::vector<int> order;
+    std::vector<PassPlan> plan;
 };
 
 namespace {
@@ -251,6 +260,75 @@ int ilog2(long long v) {
     int r = 0;
     while ((1LL << r) < v) ++r;
     return r;
+}
+
+// Execution order and passes of the forward sweep.  Without fusion every
+// gate is its own pass in circuit order.  With fusion (window of at most
+// fuse_q stored bits) the leading run of disjoint gates (first-layer
+// support) stays first and unfused; then, greedily, a pass starts with the
+// next remaining gate and takes every later remaining gate that fits in the
+// window and commutes with every remaining gate it moves past -- gates on
+// disjoint qubits commute (the gates of a brickwall layer, Sec. "Brick wall
+// circuit layout") -- up to kMaxPassGates gates.  Parity gates on the implied
+// qubit are never fused; they block their stored bit.  The product of the
+// gates in the new order is the same circuit, so f, the gradient and the HVP
+// are unchanged (up to rounding order); the backward pass walks the same
+// order in reverse.
+long long gate_bits(const GateGeom &gg) {
+    return gg.mode == rq::kParity2 ? (1LL << gg.pa) : ((1LL << gg.pa) | (1LL << gg.pb));
+}
+
+void plan_passes(rq_ctx *ctx) {
+    const int g = ctx->g;
+    ctx->order.clear();
+    ctx->plan.clear();
+    int prefix = 0;
+    if (ctx->first_layer) {
+        long long used = 0;
+        for (; prefix < g; ++prefix) {
+            const long long b = gate_bits(ctx->geo[prefix]);
+            if (used & b) break;
+            used |= b;
+        }
+    }
+    if (ctx->fuse_q <= 2) prefix = g;
+    for (int l = 0; l < prefix; ++l) {
+        ctx->plan.push_back({(int)ctx->order.size(), 1, gate_bits(ctx->geo[l])});
+        ctx->order.push_back(l);
+    }
+    std::vector<int> rest;
+    for (int l = prefix; l < g; ++l) rest.push_back(l);
+    while (!rest.empty()) {
+        const int g0 = rest[0];
+        std::vector<int> take = {g0};
+        long long W = gate_bits(ctx->geo[g0]);
+        if (ctx->geo[g0].mode != rq::kParity2) {
+            long long blocked = 0;
+            for (size_t i = 1; i < rest.size(); ++i) {
+                const GateGeom &gg = ctx->geo[rest[i]];
+                const long long b = gate_bits(gg);
+                if (gg.mode == rq::kParity2 || (b & blocked) ||
+                    __builtin_popcountll(W | b) > ctx->fuse_q || (int)take.size() >= rq::kMaxPassGates) {
+                    blocked |= b;
+                    continue;
+                }
+                take.push_back(rest[i]);
+                W |= b;
+            }
+        }
+        ctx->plan.push_back({(int)ctx->order.size(), (int)take.size(), W});
+        std::vector<int> left;
+        size_t t = 0;
+        for (int l : rest) {
+            if (t < take.size() && take[t] == l) {
+                ctx->order.push_back(l);
+                ++t;
+            } else {
+                left.push_back(l);
+            }
+        }
+        rest.swap(left);
+    }
 }
 
 // Column lists of the current range: one list (general gates) or the even-
@@ -724,6 +802,9 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
     const int nseg = (g + r - 1) / r;
     const long long set = tile * state_slots(ctx);  // one checkpoint set
     const bool backward = want_env || k > 0;
+    // fused forward passes: every checkpoint slot exists (interval 1) and a
+    // tile has whole 32-column chunks
+    const bool fused = ctx->fuse_q > 2 && r == 1 && B >= 32 && (int)ctx->plan.size() < g;
     const int n_chunks = k == 0 ? 1 : (k + ctx->kc - 1) / ctx->kc;
     for (int ch = 0; ch < n_chunks; ++ch) {
         const int d0 = ch * ctx->kc;
@@ -790,7 +871,65 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                 RQ_CUDA(cudaMemsetAsync(ctx->d_dpsi + d * set + slot0 * tile, 0, sizeof(double2) * tile, s));
             // forward pass
             long long final_slot = g;
-            if (r == 1) {
+            if (fused) {
+                // in execution order; slot p holds the state before position p
+                for (const auto &pp : ctx->plan) {
+                    if (pp.m == 1) {
+                        RQ_TRY(fwd(ctx->order[pp.pos], pp.pos, pp.pos + 1));
+                        continue;
+                    }
+                    rq::FwdFusedArgs fa{};
+                    fa.psi_in = ctx->d_psi + (long long)pp.pos * tile;
+                    fa.dpsi_in = ctx->d_dpsi + (long long)pp.pos * tile;
+                    fa.psi_base = ctx->d_psi;
+                    fa.dpsi_base = ctx->d_dpsi;
+                    fa.tile = tile;
+                    fa.dir_stride = set;
+                    fa.kdirs = kd;
+                    fa.mode = ctx->structure == 1 ? rq::kParity4 : rq::kGeneral;
+                    fa.gates = gsrc;
+                    fa.dirs = dsrc + (long long)d0 * P * 16;
+                    fa.xdir_stride = (long long)P * 16;
+                    fa.log2B = ctx->log2B;
+                    fa.log2chunks = ctx->log2B - 5;
+                    const int q = __builtin_popcountll(pp.wmask);
+                    fa.n_blocks = (ctx->n_store >> q) << fa.log2chunks;
+                    fa.outer_mask = (ctx->n_store - 1) & ~pp.wmask;
+                    fa.pass.m = pp.m;
+                    fa.pass.q = q;
+                    fa.pass.wmask = pp.wmask;
+                    double flops = 0.0;
+                    for (int j = 0; j < pp.m; ++j) {
+                        const GateGeom &geo = ctx->geo[ctx->order[pp.pos + j]];
+                        int la = 0, lb = 0;
+                        for (int b = 0, i = 0; b < 63; ++b) {
+                            if (!((pp.wmask >> b) & 1)) continue;
+                            if (b == geo.pa) la = i;
+                            if (b == geo.pb) lb = i;
+                            ++i;
+                        }
+                        fa.pass.la[j] = la;
+                        fa.pass.lb[j] = lb;
+                        fa.pass.param[j] = geo.param;
+                        // every state is a checkpoint when the backward pass
+                        // needs it; otherwise only the pass's output
+                        fa.pass.out_slot[j] = (backward || j == pp.m - 1) ? pp.pos + j + 1 : -1;
+                        const double cm = geo.mode == rq::kGeneral ? 16.0 : 8.0;
+                        flops += (double)(ctx->n_store / 4) * B * 8.0 * cm * (1 + 2 * kd);
+                    }
+                    {
+                        const double writes = backward ? pp.m : 1;
+                        ProfScope ps(ctx, kFamFwd, flops,
+                                     (double)tile * sizeof(double2) * (1 + kd) * (1.0 + writes));
+                        const long long blocks = fa.n_blocks;
+                        const int grid = (int)std::min<long long>(blocks, (long long)ctx->sms * 2);
+                        const cudaError_t le = df ? rq::launch_fwd_fused_df64(fa, grid, s)
+                                                  : rq::launch_fwd_fused(fa, grid, s);
+                        if (le != cudaSuccess) return fail(ctx, RQ_ECUDA, "fused forward pass: %s", cudaGetErrorString(le));
+                    }
+                    RQ_LAUNCHED();
+                }
+            } else if (r == 1) {
                 for (int l = 0; l < g; ++l) RQ_TRY(fwd(l, l, l + 1));
             } else {
                 int prev_len = 0;
@@ -825,8 +964,9 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
             if (!backward) continue;
             for (int d = 0; d < kd; ++d) RQ_CUDA(cudaMemsetAsync(ctx->d_dlam + d * tile, 0, sizeof(double2) * tile, s));
             const bool acc_env = want_env && first;
-            // backward step of gate l with psi_l (and its tangents) in slot sl
-            auto bwd = [&](int l, long long sl) -> rq_status {
+            // backward step of gate l, at position pos of the execution order,
+            // with the state before it (and its tangents) in slot sl
+            auto bwd = [&](int l, long long sl, int pos) -> rq_status {
                 const GateGeom &geo = ctx->geo[l];
                 rq::BwdArgs a;
                 a.lam = ctx->d_lam;
@@ -835,7 +975,7 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                 a.geo = geo;
                 a.log2B = ctx->log2B;
                 a.tile_parity = par;
-                a.update = l > 0 ? 1 : 0;
+                a.update = pos > 0 ? 1 : 0;
                 a.n_items = (geo.mode == rq::kParity2 ? ctx->n_store / 2 : ctx->n_store / 4) * B;
                 if (geo.restricted && first_layer) {
                     // E_l needs only the items where psi_{l-1} can be nonzero,
@@ -860,7 +1000,7 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                     }
                     RQ_LAUNCHED();
                 }
-                if (l > 0 || acc_env) {
+                if (pos > 0 || acc_env) {
                     a.dlam = nullptr;
                     a.dpsi = nullptr;
                     a.dir = nullptr;
@@ -878,8 +1018,10 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                 }
                 return RQ_OK;
             };
-            if (r == 1) {
-                for (int l = g - 1; l >= 0; --l) RQ_TRY(bwd(l, l));
+            if (fused) {
+                for (int pos = g - 1; pos >= 0; --pos) RQ_TRY(bwd(ctx->order[pos], pos, pos));
+            } else if (r == 1) {
+                for (int l = g - 1; l >= 0; --l) RQ_TRY(bwd(l, l, l));
             } else {
                 for (int sg = nseg - 1; sg >= 0; --sg) {
                     const int base = sg * r, len = std::min(r, g - base);
@@ -887,7 +1029,7 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                         RQ_TRY(copy_slot(sg, nseg));
                         for (int i = 0; i < len; ++i) RQ_TRY(fwd(base + i, nseg + i, nseg + i + 1));
                     }
-                    for (int l = base + len - 1; l >= base; --l) RQ_TRY(bwd(l, nseg + (l - base)));
+                    for (int l = base + len - 1; l >= base; --l) RQ_TRY(bwd(l, nseg + (l - base), l));
                 }
             }
             if (acc_env) {
@@ -1237,6 +1379,7 @@ rq_status rq_setup_target(rq_ctx *ctx, const rq_target *tgt, const rq_circuit *c
                          ctx->stream) != cudaSuccess ||
          cudaStreamSynchronize(ctx->stream) != cudaSuccess))
         st = fail(ctx, RQ_ECUDA, "copy of param_of failed");
+    plan_passes(ctx);
     ctx->c0 = 0;
     ctx->c1 = 1LL << ctx->n;
     ctx->tshift = 0;
@@ -1531,7 +1674,33 @@ rq_status rq_set_checkpointing(rq_ctx *ctx, int interval) {
 rq_status rq_set_first_layer(rq_ctx *ctx, int enable) {
     if (!ctx) return RQ_EINVAL;
     ctx->first_layer = enable != 0;
+    if (ctx->ready) plan_passes(ctx);
     ++ctx->version;
+    return RQ_OK;
+}
+
+rq_status rq_set_fusion(rq_ctx *ctx, int max_window_qubits) {
+    if (!ctx) return RQ_EINVAL;
+    if (max_window_qubits != 0 && (max_window_qubits < 3 || max_window_qubits > rq::kMaxWindow))
+        return fail(ctx, RQ_EINVAL, "fusion window %d is neither 0 (off) nor in [3, %d]", max_window_qubits,
+                    rq::kMaxWindow);
+    ctx->fuse_q = max_window_qubits;
+    if (ctx->ready) plan_passes(ctx);
+    ++ctx->version;
+    return RQ_OK;
+}
+
+rq_status rq_fusion_info(const rq_ctx *ctx, int *n_passes, int *fused_gates, int *max_pass_gates) {
+    if (!ctx) return RQ_EINVAL;
+    int np = 0, fg = 0, mx = 0;
+    for (const auto &pp : ctx->plan) {
+        ++np;
+        if (pp.m > 1) fg += pp.m;
+        mx = std::max(mx, pp.m);
+    }
+    if (n_passes) *n_passes = np;
+    if (fused_gates) *fused_gates = fg;
+    if (max_pass_gates) *max_pass_gates = mx;
     return RQ_OK;
 }
 

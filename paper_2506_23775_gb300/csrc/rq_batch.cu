@@ -12,7 +12,9 @@
 //
 // The columns-per-tile of every problem is autotuned: candidate tile caps
 // that fit the device memory are timed on a captured cost-only evaluation of
-// the whole batch and the fastest is kept.
+// the whole batch and the fastest is kept.  Then the fusion window of the
+// forward passes (gates per pass, rq_set_fusion: off, 4, 5 or 6 stored
+// qubits) is tuned the same way at that tile, unless the caller fixed it.
 #include "rq_internal.h"
 
 #include <algorithm>
@@ -30,6 +32,7 @@ struct rq_batch {
     std::vector<long long> goff;   // complex offset of each problem's gates
     long long gtotal = 0;          // sum of n_params * 16
     int tile_cap = 0;              // 0: autotune
+    bool tile_fixed = false;       // the caller set the tile (rq_batch_set_tile)
     bool tuned = false;
     double2 *d_gates = nullptr, *d_dirs = nullptr, *d_rgrad = nullptr, *d_hvps = nullptr;
     double *d_f = nullptr;
@@ -39,6 +42,9 @@ struct rq_batch {
     cudaEvent_t fork = nullptr;
     std::vector<cudaEvent_t> joins;
     std::vector<double> tune_ms;   // per candidate cap 64, 128, 256, 512 (-1: skipped)
+    int fuse_req = -1;             // fusion window for every problem; -1: autotune
+    int fuse_q = 0;                // the window in use
+    std::vector<double> fuse_ms;   // per candidate window 0, 4, 5, 6 (-1: not timed)
 };
 
 namespace {
@@ -172,6 +178,16 @@ rq_status apply_cap(rq_batch *b, int cap) {
     return RQ_OK;
 }
 
+rq_status apply_fusion(rq_batch *b, int q) {
+    for (rq_ctx *c : b->ctxs) {
+        const rq_status st = rq_set_fusion(c, q);
+        if (st != RQ_OK) return ctx_fail(b, c, st);
+    }
+    b->fuse_q = q;
+    drop_graph(b);
+    return RQ_OK;
+}
+
 // Time each feasible tile cap on a captured cost-only evaluation; keep the best.
 rq_status autotune(rq_batch *b) {
     const int caps[4] = {64, 128, 256, 512};
@@ -192,7 +208,7 @@ rq_status autotune(rq_batch *b) {
     cudaEvent_t e0, e1;
     RB_CUDA(cudaEventCreate(&e0));
     RB_CUDA(cudaEventCreate(&e1));
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 4 && !b->tile_fixed; ++i) {
         double need = 0;
         for (size_t p = 0; p < b->ctxs.size(); ++p)
             need += (double)rq::workspace_bytes_for(b->ctxs[p], std::min(caps[i], pow2ceil(1LL << b->n[p])), 1);
@@ -217,12 +233,49 @@ rq_status autotune(rq_batch *b) {
             best = caps[i];
         }
     }
+    if (b->tile_fixed) best = b->tile_cap;
+    if (best < 0) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return bfail(b, RQ_ENOMEM, "no tile size fits the batch in device memory");
+    }
+    b->tile_cap = best;
+    rq_status st = apply_cap(b, best);
+    // gates per pass: the fusion window, timed on the same cost-only proxy
+    const int wins[4] = {0, 4, 5, 6};
+    b->fuse_ms.assign(4, -1.0);
+    if (st == RQ_OK && b->fuse_req < 0) {
+        int best_q = 0;
+        double best_q_ms = 1e300;
+        for (int i = 0; i < 4 && st == RQ_OK; ++i) {
+            st = apply_fusion(b, wins[i]);
+            if (st == RQ_OK) st = capture(b, 0, 0);
+            if (st != RQ_OK) break;
+            cudaGraphLaunch(b->exec, b->main);  // warm-up
+            cudaEventRecord(e0, b->main);
+            cudaGraphLaunch(b->exec, b->main);
+            cudaEventRecord(e1, b->main);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                st = bfail(b, RQ_ECUDA, "fusion autotune: %s", cudaGetErrorString(cudaGetLastError()));
+                break;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            b->fuse_ms[i] = ms;
+            if (ms < best_q_ms) {
+                best_q_ms = ms;
+                best_q = wins[i];
+            }
+        }
+        if (st == RQ_OK) st = apply_fusion(b, best_q);
+    } else if (st == RQ_OK) {
+        st = apply_fusion(b, b->fuse_req);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (best < 0) return bfail(b, RQ_ENOMEM, "no tile size fits the batch in device memory");
-    b->tile_cap = best;
+    if (st != RQ_OK) return st;
     b->tuned = true;
-    return apply_cap(b, best);
+    return RQ_OK;
 }
 
 }  // namespace
@@ -284,6 +337,12 @@ rq_status rq_batch_add(rq_batch *b, const rq_target *t, const rq_circuit *c, int
         rq_destroy(ctx);
         return st;
     }
+    st = rq_set_fusion(ctx, b->fuse_q);  // the batch's current window
+    if (st != RQ_OK) {
+        bfail(b, st, "problem %zu: %s", b->ctxs.size(), rq_last_error(ctx));
+        rq_destroy(ctx);
+        return st;
+    }
     cudaEvent_t ev;
     RB_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     if (index) *index = (int)b->ctxs.size();
@@ -294,7 +353,6 @@ rq_status rq_batch_add(rq_batch *b, const rq_target *t, const rq_circuit *c, int
     b->goff.push_back(b->gtotal);
     b->gtotal += (long long)inf.n_params * 16;
     b->cap_k = -1;
-    b->tuned = b->tile_cap > 0;
     drop_graph(b);
     return RQ_OK;
 }
@@ -304,7 +362,8 @@ rq_status rq_batch_set_tile(rq_batch *b, int columns_per_tile) {
     if (columns_per_tile < 0 || (columns_per_tile & (columns_per_tile - 1)) != 0)
         return bfail(b, RQ_EINVAL, "columns_per_tile %d is not 0 or a power of two", columns_per_tile);
     b->tile_cap = columns_per_tile;
-    b->tuned = columns_per_tile > 0;
+    b->tile_fixed = columns_per_tile > 0;
+    b->tuned = columns_per_tile > 0 && b->fuse_req >= 0;  // else the fusion window is tuned at the next evaluation
     if (columns_per_tile > 0) return apply_cap(b, columns_per_tile);
     return RQ_OK;
 }
@@ -353,6 +412,28 @@ rq_status rq_batch_info(const rq_batch *b, int *n_problems, int *columns_per_til
     if (columns_per_tile) *columns_per_tile = b->tile_cap;
     if (tune_ms)
         for (int i = 0; i < 4; ++i) tune_ms[i] = i < (int)b->tune_ms.size() ? b->tune_ms[i] : -1.0;
+    return RQ_OK;
+}
+
+rq_status rq_batch_set_fusion(rq_batch *b, int max_window_qubits) {
+    if (!b) return RQ_EINVAL;
+    if (max_window_qubits != -1 && max_window_qubits != 0 && (max_window_qubits < 3 || max_window_qubits > rq::kMaxWindow))
+        return bfail(b, RQ_EINVAL, "fusion window %d is neither -1 (autotune), 0 (off) nor in [3, %d]",
+                     max_window_qubits, rq::kMaxWindow);
+    b->fuse_req = max_window_qubits;
+    if (max_window_qubits >= 0) {
+        b->fuse_ms.assign(4, -1.0);
+        return apply_fusion(b, max_window_qubits);
+    }
+    b->tuned = false;  // tune again at the next evaluation
+    return RQ_OK;
+}
+
+rq_status rq_batch_fusion_info(const rq_batch *b, int *window, double *tune_ms) {
+    if (!b) return RQ_EINVAL;
+    if (window) *window = b->fuse_q;
+    if (tune_ms)
+        for (int i = 0; i < 4; ++i) tune_ms[i] = i < (int)b->fuse_ms.size() ? b->fuse_ms[i] : -1.0;
     return RQ_OK;
 }
 

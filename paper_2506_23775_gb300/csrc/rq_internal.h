@@ -75,6 +75,40 @@ struct BwdArgs {
     const int32_t *cols = nullptr;  // column basis states (-1: padding) when geo.restricted
 };
 
+// One fused forward pass (window fusion): m consecutive gates of the
+// execution order that all act within a window of q stored bits are applied
+// to blocks of [2^q amplitudes x 32 columns] held in shared memory, so the
+// state is read from HBM once per pass instead of once per gate.
+constexpr int kMaxWindow = 6;      // window bits (2^6 rows x 32 columns per block)
+constexpr int kMaxPassGates = 16;  // gates per fused pass
+struct FusedPass {
+    int m = 0, q = 0;
+    long long wmask = 0;              // stored bits of the window
+    int la[kMaxPassGates];            // window-local bit of the gate's first listed qubit (geo.pa)
+    int lb[kMaxPassGates];            // ... of its second listed qubit (geo.pb)
+    int param[kMaxPassGates];         // parameter gate index
+    int out_slot[kMaxPassGates];      // checkpoint slot written after the gate (-1: none)
+};
+
+struct FwdFusedArgs {
+    const double2 *psi_in;      // state before the pass (tile)
+    const double2 *dpsi_in;     // tangent of direction 0 before the pass; direction d at + d * dir_stride
+    double2 *psi_base;          // checkpoint slot 0 (slot s at + s * tile)
+    double2 *dpsi_base;         // tangent slot 0 of direction 0
+    long long tile;             // elements per slot
+    long long dir_stride;       // elements between directions' checkpoint sets
+    int kdirs;
+    int mode;                   // kGeneral or kParity4 (every gate of the pass)
+    const double2 *gates;       // parameter gates [P][16]
+    const double2 *dirs;        // direction d of parameter p at dirs + d * xdir_stride + p * 16
+    long long xdir_stride;
+    int log2B;
+    int log2chunks;             // log2(B / 32)
+    long long n_blocks;         // (n_store >> q) << log2chunks
+    long long outer_mask;       // stored bits outside the window
+    FusedPass pass;
+};
+
 // Sector tables of the stored target.
 struct TargetDev {
     const int32_t *sec_of;      // [2^n] sector id of a basis index
@@ -93,6 +127,9 @@ void launch_bwd_base(const BwdArgs &a, int grid, cudaStream_t s);
 void launch_bwd_dir(const BwdArgs &a, int grid, cudaStream_t s);
 void launch_init_unit(double2 *psi0, const int32_t *cols, int B, int log2B, long long n_store,
                       int parity_layout, cudaStream_t s);
+// Fused forward pass (shared-memory bytes of the launch from fused_smem_bytes).
+size_t fused_smem_bytes(int q, int kdirs, int m, int df64);
+cudaError_t launch_fwd_fused(const FwdFusedArgs &a, int grid, cudaStream_t s);
 
 // Launchers (rq_sweep_df64.cu): the same steps in double-float arithmetic;
 // tiles, gates and directions hold float4 (hi, lo, hi, lo) in the same bytes.
@@ -101,6 +138,7 @@ void launch_bwd_base_df64(const BwdArgs &a, int grid, cudaStream_t s);
 void launch_bwd_dir_df64(const BwdArgs &a, int grid, cudaStream_t s);
 void launch_init_unit_df64(double2 *psi0, const int32_t *cols, int B, int log2B, long long n_store, cudaStream_t s);
 void launch_to_df64(const double2 *in, double2 *out, long long n, cudaStream_t s);
+cudaError_t launch_fwd_fused_df64(const FwdFusedArgs &a, int grid, cudaStream_t s);
 void launch_scatter_target_df64(const TargetDev &t, const int32_t *cols, const double *wts, int B, int log2B,
                                 int parity_layout, int n, double2 *lam, const double2 *psi_final, double *fpart,
                                 cudaStream_t s);

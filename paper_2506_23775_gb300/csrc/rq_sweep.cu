@@ -671,6 +671,120 @@ __global__ void __launch_bounds__(kThreads, MODE == kGeneral ? 1 : 2) k_bwd_dir(
     block_reduce_store(E, a.part + (long long)blockIdx.x * kEnvDoubles);
 }
 
+// ------------------------------------------------------ fused forward pass --
+//
+// Window fusion (Sec. "Brick wall circuit layout": the gates of a layer are
+// disjoint and commute, so consecutive gates inside a small set of qubits can
+// be applied together): a CTA copies a block of [2^q amplitudes x 32 columns]
+// -- the amplitudes that differ only in the window's q stored bits, for 32
+// consecutive columns -- into shared memory, applies the pass's m gates (and
+// their tangent steps) there, and writes a gate's output to HBM only where a
+// checkpoint slot is wanted (every gate when the backward pass needs the
+// states, the last one otherwise).  Same arithmetic per item as k_fwd.
+// Shared memory: (1 + KD) state blocks, the gates' tables, a row -> stored
+// offset table.
+
+size_t fused_bytes(int q, int kd, int m) {
+    return (size_t)(1 + kd) * ((size_t)32 << q) * sizeof(double2) + (size_t)(1 + kd) * m * sizeof(Mat3) +
+           ((size_t)1 << q) * sizeof(long long);
+}
+
+template <int MODE, int KD>
+__global__ void __launch_bounds__(kThreads, 1) k_fwd_fused(const FwdFusedArgs a) {
+    extern __shared__ __align__(16) unsigned char fused_raw[];
+    const FusedPass &p = a.pass;
+    const int rows = 1 << p.q, m = p.m;
+    const int elems = rows * 32, items = (rows >> 2) * 32;
+    double2 *S = reinterpret_cast<double2 *>(fused_raw);             // [1 + KD][rows][32]
+    Mat3 *mg = reinterpret_cast<Mat3 *>(S + (1 + KD) * elems);       // [m]
+    Mat3 *mx = mg + m;                                                // [KD][m]
+    long long *rowoff = reinterpret_cast<long long *>(mx + KD * m);  // [rows]
+    for (int e = threadIdx.x; e < m * 16; e += blockDim.x) {
+        const int j = e >> 4;
+        tabulate3(mg[j], a.gates + (long long)p.param[j] * 16, e & 15, 0);
+#pragma unroll
+        for (int d = 0; d < KD; ++d)
+            tabulate3(mx[d * m + j], a.dirs + d * a.xdir_stride + (long long)p.param[j] * 16, e & 15, 0);
+    }
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) rowoff[r] = deposit_bits(r, p.wmask);
+    __syncthreads();
+    const long long cmask = (1LL << a.log2chunks) - 1;
+    for (long long blk = blockIdx.x; blk < a.n_blocks; blk += gridDim.x) {
+        const long long x0 = deposit_bits(blk >> a.log2chunks, a.outer_mask);
+        const long long col0 = (blk & cmask) << 5;
+        for (int e = threadIdx.x; e < elems; e += blockDim.x) {
+            const long long off = ((x0 | rowoff[e >> 5]) << a.log2B) | (col0 + (e & 31));
+            S[e] = __ldg(&a.psi_in[off]);
+#pragma unroll
+            for (int d = 0; d < KD; ++d) S[(1 + d) * elems + e] = __ldg(&a.dpsi_in[d * a.dir_stride + off]);
+        }
+        __syncthreads();
+        for (int j = 0; j < m; ++j) {
+            const int la = p.la[j], lb = p.lb[j];
+            const int lo = la < lb ? la : lb, hi = la < lb ? lb : la;
+            const int slot = p.out_slot[j];
+            for (int it = threadIdx.x; it < items; it += blockDim.x) {
+                const int col = it & 31;
+                const int r0 = (int)insert_zero(insert_zero(it >> 5, lo), hi);
+                const int rw[4] = {r0, r0 | (1 << lb), r0 | (1 << la), r0 | (1 << la) | (1 << lb)};
+                Amp3 x[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) x[c] = amp3(S[rw[c] * 32 + col]);
+                double2 y[4];
+                if constexpr (MODE == kGeneral) matvec3(mg[j], x, y);
+                else matvec3_blocks(mg[j], x, y);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) S[rw[c] * 32 + col] = y[c];
+                if (slot >= 0) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        a.psi_base[slot * a.tile + (((x0 | rowoff[rw[c]]) << a.log2B) | (col0 + col))] = y[c];
+                }
+#pragma unroll
+                for (int d = 0; d < KD; ++d) {
+                    double2 *T = S + (1 + d) * elems;
+                    Amp3 t[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) t[c] = amp3(T[rw[c] * 32 + col]);
+                    if constexpr (MODE == kGeneral) matvec3_pair(mg[j], t, mx[d * m + j], x, y);  // G psi' + X psi
+                    else matvec3_pair_blocks(mg[j], t, mx[d * m + j], x, y);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) T[rw[c] * 32 + col] = y[c];
+                    if (slot >= 0) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            a.dpsi_base[d * a.dir_stride + slot * a.tile +
+                                        (((x0 | rowoff[rw[c]]) << a.log2B) | (col0 + col))] = y[c];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <int MODE>
+cudaError_t launch_fused_mode(const FwdFusedArgs &a, int grid, size_t smem, cudaStream_t s) {
+    switch (a.kdirs) {
+        case 0: k_fwd_fused<MODE, 0><<<grid, kThreads, smem, s>>>(a); break;
+        case 1: k_fwd_fused<MODE, 1><<<grid, kThreads, smem, s>>>(a); break;
+        case 2: k_fwd_fused<MODE, 2><<<grid, kThreads, smem, s>>>(a); break;
+        case 3: k_fwd_fused<MODE, 3><<<grid, kThreads, smem, s>>>(a); break;
+        default: k_fwd_fused<MODE, 4><<<grid, kThreads, smem, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t fused_attributes(int bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k_fwd_fused<MODE, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_fused<MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_fused<MODE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_fused<MODE, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_fused<MODE, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
 // psi_0 = |j_b> for every column b of the tile (the tile is zeroed before).
 __global__ void k_init_unit(double2 *psi0, const int32_t *cols, int B, int log2B, long long mask) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -707,15 +821,30 @@ void launch_bwd_dir(const BwdArgs &a, int grid, cudaStream_t s) {
     }
 }
 
+size_t fused_smem_bytes(int q, int kdirs, int m, int df64) {
+    (void)df64;  // double-float blocks and tables take the same bytes (float4 amplitudes, float2 triples)
+    return fused_bytes(q, kdirs, m);
+}
+
+cudaError_t launch_fwd_fused(const FwdFusedArgs &a, int grid, cudaStream_t s) {
+    const size_t smem = fused_bytes(a.pass.q, a.kdirs, a.pass.m);
+    return a.mode == kGeneral ? launch_fused_mode<kGeneral>(a, grid, smem, s)
+                              : launch_fused_mode<kParity4>(a, grid, smem, s);
+}
+
 cudaError_t init_sweep_attributes() {
     // the pipelined kernels keep two stages of item slots in dynamic shared
-    // memory (128 KB per CTA for k_bwd_dir, 64 KB for k_bwd_base)
+    // memory (128 KB per CTA for k_bwd_dir, 64 KB for k_bwd_base); the fused
+    // forward passes up to their largest block and tables
     cudaError_t e = cudaFuncSetAttribute(k_bwd_dir<kGeneral>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kDirSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_bwd_base<kGeneral>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBaseSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_bwd_base<kParity4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBaseSmem);
+    const int fmax = (int)fused_bytes(kMaxWindow, kMaxDirs, kMaxPassGates);
+    if (e == cudaSuccess) e = fused_attributes<kGeneral>(fmax);
+    if (e == cudaSuccess) e = fused_attributes<kParity4>(fmax);
     return e;
 }
 

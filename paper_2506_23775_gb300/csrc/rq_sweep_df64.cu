@@ -149,6 +149,79 @@ __device__ __forceinline__ AmpDf3 amp_df3(const float4 x) {
     return r;
 }
 
+// Local indices that a parity gate couples within its even block {0, 3} and
+// odd block {1, 2}: out[i] = sum over c in block(i).
+__device__ __forceinline__ int blk(int i, int u) {
+    // u = 0, 1: the two members of i's block
+    return (i == 0 || i == 3) ? (u == 0 ? 0 : 3) : (u == 0 ? 1 : 2);
+}
+
+// y = G x for a general gate in the three-product form (rows finished).
+__device__ __forceinline__ void df_matvec3(const MatDf3 &m, const AmpDf3 (&x)[4], float4 (&y)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        Acc k;
+        acc_set(k, x[0].uh, x[0].ul, m.s[i * 4].x, m.s[i * 4].y);
+#pragma unroll
+        for (int c = 1; c < 4; ++c) acc_mac(k, x[c].uh, x[c].ul, m.s[i * 4 + c].x, m.s[i * 4 + c].y);
+        CAcc q{k, k};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            acc_mac(q.re, m.nb[i * 4 + c].x, m.nb[i * 4 + c].y, x[c].S.x, x[c].S.y);
+            acc_mac(q.im, m.a[i * 4 + c].x, m.a[i * 4 + c].y, x[c].D.x, x[c].D.y);
+        }
+        y[i] = fin(q);
+    }
+}
+
+// y = G t + X x (a tangent step), three-product form.
+__device__ __forceinline__ void df_matvec3_pair(const MatDf3 &m, const AmpDf3 (&t)[4], const MatDf3 &n,
+                                                const AmpDf3 (&x)[4], float4 (&y)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        Acc k;
+        acc_set(k, t[0].uh, t[0].ul, m.s[i * 4].x, m.s[i * 4].y);
+#pragma unroll
+        for (int c = 1; c < 4; ++c) acc_mac(k, t[c].uh, t[c].ul, m.s[i * 4 + c].x, m.s[i * 4 + c].y);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc_mac(k, x[c].uh, x[c].ul, n.s[i * 4 + c].x, n.s[i * 4 + c].y);
+        CAcc q{k, k};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            acc_mac(q.re, m.nb[i * 4 + c].x, m.nb[i * 4 + c].y, t[c].S.x, t[c].S.y);
+            acc_mac(q.re, n.nb[i * 4 + c].x, n.nb[i * 4 + c].y, x[c].S.x, x[c].S.y);
+            acc_mac(q.im, m.a[i * 4 + c].x, m.a[i * 4 + c].y, t[c].D.x, t[c].D.y);
+            acc_mac(q.im, n.a[i * 4 + c].x, n.a[i * 4 + c].y, x[c].D.x, x[c].D.y);
+        }
+        y[i] = fin(q);
+    }
+}
+
+// y = G p for a parity gate on two stored qubits (two terms per row).
+__device__ __forceinline__ void df_blocks(const float4 *g, const float4 (&p)[4], float4 (&y)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        CAcc q;
+        cset(q, g[i * 4 + blk(i, 0)], p[blk(i, 0)]);
+        cmac(q, g[i * 4 + blk(i, 1)], p[blk(i, 1)]);
+        y[i] = fin(q);
+    }
+}
+
+// y = G t + X p for a parity gate on two stored qubits.
+__device__ __forceinline__ void df_blocks_pair(const float4 *g, const float4 (&t)[4], const float4 *xm,
+                                               const float4 (&p)[4], float4 (&y)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        CAcc q;
+        cset(q, g[i * 4 + blk(i, 0)], t[blk(i, 0)]);
+        cmac(q, g[i * 4 + blk(i, 1)], t[blk(i, 1)]);
+        cmac(q, xm[i * 4 + blk(i, 0)], p[blk(i, 0)]);
+        cmac(q, xm[i * 4 + blk(i, 1)], p[blk(i, 1)]);
+        y[i] = fin(q);
+    }
+}
+
 __device__ __forceinline__ void offsets2(long long r, long long b, int p, int qfirst, int parity, int log2B,
                                          long long (&off)[2], int &i0, int &i1) {
     const long long y0 = insert_zero(r, p);
@@ -165,13 +238,6 @@ __device__ __forceinline__ void offsets2(long long r, long long b, int p, int qf
         i0 = 2;
         i1 = 1;
     }
-}
-
-// Local indices that a parity gate couples within its even block {0, 3} and
-// odd block {1, 2}: out[i] = sum over c in block(i).
-__device__ __forceinline__ int blk(int i, int u) {
-    // u = 0, 1: the two members of i's block
-    return (i == 0 || i == 3) ? (u == 0 ? 0 : 3) : (u == 0 ? 1 : 2);
 }
 
 __device__ __forceinline__ void block_reduce_store(const CAcc (&acc)[16], double *out) {
@@ -234,45 +300,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_fwd_df(const FwdArgs a) {
             AmpDf3 x[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) x[c] = amp_df3(__ldg(&psi_in[off[c]]));
+            float4 y[4];
+            df_matvec3(sg3, x, y);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                Acc k;
-                acc_set(k, x[0].uh, x[0].ul, sg3.s[i * 4].x, sg3.s[i * 4].y);
-#pragma unroll
-                for (int c = 1; c < 4; ++c) acc_mac(k, x[c].uh, x[c].ul, sg3.s[i * 4 + c].x, sg3.s[i * 4 + c].y);
-                CAcc q{k, k};
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    acc_mac(q.re, sg3.nb[i * 4 + c].x, sg3.nb[i * 4 + c].y, x[c].S.x, x[c].S.y);
-                    acc_mac(q.im, sg3.a[i * 4 + c].x, sg3.a[i * 4 + c].y, x[c].D.x, x[c].D.y);
-                }
-                psi_out[off[i]] = fin(q);
-            }
+            for (int i = 0; i < 4; ++i) psi_out[off[i]] = y[i];
             for (int d = 0; d < a.kdirs; ++d) {
                 const float4 *din = dpsi_in + d * a.dir_stride;
                 float4 *dout = dpsi_out + d * a.dir_stride;
                 AmpDf3 t[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) t[c] = amp_df3(__ldg(&din[off[c]]));
+                df_matvec3_pair(sg3, t, sx3[d], x, y);  // G psi' + X psi
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {  // G psi' + X psi
-                    Acc k;
-                    acc_set(k, t[0].uh, t[0].ul, sg3.s[i * 4].x, sg3.s[i * 4].y);
-#pragma unroll
-                    for (int c = 1; c < 4; ++c) acc_mac(k, t[c].uh, t[c].ul, sg3.s[i * 4 + c].x, sg3.s[i * 4 + c].y);
-#pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        acc_mac(k, x[c].uh, x[c].ul, sx3[d].s[i * 4 + c].x, sx3[d].s[i * 4 + c].y);
-                    CAcc q{k, k};
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        acc_mac(q.re, sg3.nb[i * 4 + c].x, sg3.nb[i * 4 + c].y, t[c].S.x, t[c].S.y);
-                        acc_mac(q.re, sx3[d].nb[i * 4 + c].x, sx3[d].nb[i * 4 + c].y, x[c].S.x, x[c].S.y);
-                        acc_mac(q.im, sg3.a[i * 4 + c].x, sg3.a[i * 4 + c].y, t[c].D.x, t[c].D.y);
-                        acc_mac(q.im, sx3[d].a[i * 4 + c].x, sx3[d].a[i * 4 + c].y, x[c].D.x, x[c].D.y);
-                    }
-                    dout[off[i]] = fin(q);
-                }
+                for (int i = 0; i < 4; ++i) dout[off[i]] = y[i];
             }
         } else if constexpr (MODE == kParity4) {
             long long off[4];
@@ -280,42 +320,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_fwd_df(const FwdArgs a) {
             float4 p[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) p[c] = __ldg(&psi_in[off[c]]);
+            float4 y[4];
+            df_blocks(sg, p, y);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                CAcc q;
-                if (MODE == kGeneral) {
-                    cset(q, sg[i * 4 + 0], p[0]);
-#pragma unroll
-                    for (int c = 1; c < 4; ++c) cmac(q, sg[i * 4 + c], p[c]);
-                } else {
-                    cset(q, sg[i * 4 + blk(i, 0)], p[blk(i, 0)]);
-                    cmac(q, sg[i * 4 + blk(i, 1)], p[blk(i, 1)]);
-                }
-                psi_out[off[i]] = fin(q);
-            }
+            for (int i = 0; i < 4; ++i) psi_out[off[i]] = y[i];
             for (int d = 0; d < a.kdirs; ++d) {
                 const float4 *din = dpsi_in + d * a.dir_stride;
                 float4 *dout = dpsi_out + d * a.dir_stride;
                 float4 t[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) t[c] = __ldg(&din[off[c]]);
+                df_blocks_pair(sg, t, sx[d], p, y);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    CAcc q;
-                    if (MODE == kGeneral) {
-                        cset(q, sg[i * 4 + 0], t[0]);
-#pragma unroll
-                        for (int c = 1; c < 4; ++c) cmac(q, sg[i * 4 + c], t[c]);
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) cmac(q, sx[d][i * 4 + c], p[c]);
-                    } else {
-                        cset(q, sg[i * 4 + blk(i, 0)], t[blk(i, 0)]);
-                        cmac(q, sg[i * 4 + blk(i, 1)], t[blk(i, 1)]);
-                        cmac(q, sx[d][i * 4 + blk(i, 0)], p[blk(i, 0)]);
-                        cmac(q, sx[d][i * 4 + blk(i, 1)], p[blk(i, 1)]);
-                    }
-                    dout[off[i]] = fin(q);
-                }
+                for (int i = 0; i < 4; ++i) dout[off[i]] = y[i];
             }
         } else {  // kParity2
             long long off[2];
@@ -833,6 +850,136 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_base_df2(const BwdArgs a) {
     block_reduce_store_half(E, a.part + (long long)blockIdx.x * kEnvDoubles);
 }
 
+// ------------------------------------------------------ fused forward pass --
+//
+// The double-float form of the fused forward pass of rq_sweep.cu: blocks of
+// [2^q amplitudes x 32 columns] in shared memory, the pass's gates applied
+// there with the same item arithmetic as k_fwd_df, outputs written where a
+// checkpoint slot is wanted.  Per gate a 384-byte table: MatDf3 (general) or
+// the 16 raw entries (parity gates on two stored qubits).
+constexpr int kTabBytes = 384;
+static_assert(sizeof(MatDf3) <= kTabBytes && 16 * sizeof(float4) <= kTabBytes, "gate table size");
+
+template <int MODE, int KD>
+__global__ void __launch_bounds__(kThreads, 1) k_fwd_fused_df(const FwdFusedArgs a) {
+    extern __shared__ __align__(16) unsigned char fused_raw[];
+    const FusedPass &p = a.pass;
+    const int rows = 1 << p.q, m = p.m;
+    const int elems = rows * 32, items = (rows >> 2) * 32;
+    float4 *S = reinterpret_cast<float4 *>(fused_raw);                      // [1 + KD][rows][32]
+    unsigned char *tab = reinterpret_cast<unsigned char *>(S + (1 + KD) * elems);  // [(1 + KD) m][kTabBytes]
+    long long *rowoff = reinterpret_cast<long long *>(tab + (size_t)(1 + KD) * m * kTabBytes);
+    const float4 *gates = reinterpret_cast<const float4 *>(a.gates);
+    const float4 *dirs = reinterpret_cast<const float4 *>(a.dirs);
+    auto gtab = [&](int t) { return tab + (size_t)t * kTabBytes; };
+    for (int e = threadIdx.x; e < m * 16; e += blockDim.x) {
+        const int j = e >> 4, c = e & 15;
+        const float4 *g = gates + (long long)p.param[j] * 16;
+        if (MODE == kGeneral) tabulate_df3(*reinterpret_cast<MatDf3 *>(gtab(j)), g, c);
+        else reinterpret_cast<float4 *>(gtab(j))[c] = g[c];
+#pragma unroll
+        for (int d = 0; d < KD; ++d) {
+            const float4 *x = dirs + d * a.xdir_stride + (long long)p.param[j] * 16;
+            if (MODE == kGeneral) tabulate_df3(*reinterpret_cast<MatDf3 *>(gtab((1 + d) * m + j)), x, c);
+            else reinterpret_cast<float4 *>(gtab((1 + d) * m + j))[c] = x[c];
+        }
+    }
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) rowoff[r] = deposit_bits(r, p.wmask);
+    __syncthreads();
+    const float4 *psi_in = reinterpret_cast<const float4 *>(a.psi_in);
+    const float4 *dpsi_in = reinterpret_cast<const float4 *>(a.dpsi_in);
+    float4 *psi_base = reinterpret_cast<float4 *>(a.psi_base);
+    float4 *dpsi_base = reinterpret_cast<float4 *>(a.dpsi_base);
+    const long long cmask = (1LL << a.log2chunks) - 1;
+    for (long long blk = blockIdx.x; blk < a.n_blocks; blk += gridDim.x) {
+        const long long x0 = deposit_bits(blk >> a.log2chunks, a.outer_mask);
+        const long long col0 = (blk & cmask) << 5;
+        for (int e = threadIdx.x; e < elems; e += blockDim.x) {
+            const long long off = ((x0 | rowoff[e >> 5]) << a.log2B) | (col0 + (e & 31));
+            S[e] = __ldg(&psi_in[off]);
+#pragma unroll
+            for (int d = 0; d < KD; ++d) S[(1 + d) * elems + e] = __ldg(&dpsi_in[d * a.dir_stride + off]);
+        }
+        __syncthreads();
+        for (int j = 0; j < m; ++j) {
+            const int la = p.la[j], lb = p.lb[j];
+            const int lo = la < lb ? la : lb, hi = la < lb ? lb : la;
+            const int slot = p.out_slot[j];
+            for (int it = threadIdx.x; it < items; it += blockDim.x) {
+                const int col = it & 31;
+                const int r0 = (int)insert_zero(insert_zero(it >> 5, lo), hi);
+                const int rw[4] = {r0, r0 | (1 << lb), r0 | (1 << la), r0 | (1 << la) | (1 << lb)};
+                float4 v[4], y[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) v[c] = S[rw[c] * 32 + col];
+                AmpDf3 x[4];
+                if constexpr (MODE == kGeneral) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) x[c] = amp_df3(v[c]);
+                    df_matvec3(*reinterpret_cast<const MatDf3 *>(gtab(j)), x, y);
+                } else {
+                    df_blocks(reinterpret_cast<const float4 *>(gtab(j)), v, y);
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) S[rw[c] * 32 + col] = y[c];
+                if (slot >= 0) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        psi_base[slot * a.tile + (((x0 | rowoff[rw[c]]) << a.log2B) | (col0 + col))] = y[c];
+                }
+#pragma unroll
+                for (int d = 0; d < KD; ++d) {
+                    float4 *T = S + (1 + d) * elems;
+                    if constexpr (MODE == kGeneral) {
+                        AmpDf3 t[4];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) t[c] = amp_df3(T[rw[c] * 32 + col]);
+                        df_matvec3_pair(*reinterpret_cast<const MatDf3 *>(gtab(j)), t,
+                                        *reinterpret_cast<const MatDf3 *>(gtab((1 + d) * m + j)), x, y);
+                    } else {
+                        float4 t[4];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) t[c] = T[rw[c] * 32 + col];
+                        df_blocks_pair(reinterpret_cast<const float4 *>(gtab(j)), t,
+                                       reinterpret_cast<const float4 *>(gtab((1 + d) * m + j)), v, y);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) T[rw[c] * 32 + col] = y[c];
+                    if (slot >= 0) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            dpsi_base[d * a.dir_stride + slot * a.tile +
+                                      (((x0 | rowoff[rw[c]]) << a.log2B) | (col0 + col))] = y[c];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <int MODE>
+cudaError_t launch_fused_df_mode(const FwdFusedArgs &a, int grid, size_t smem, cudaStream_t s) {
+    switch (a.kdirs) {
+        case 0: k_fwd_fused_df<MODE, 0><<<grid, kThreads, smem, s>>>(a); break;
+        case 1: k_fwd_fused_df<MODE, 1><<<grid, kThreads, smem, s>>>(a); break;
+        case 2: k_fwd_fused_df<MODE, 2><<<grid, kThreads, smem, s>>>(a); break;
+        case 3: k_fwd_fused_df<MODE, 3><<<grid, kThreads, smem, s>>>(a); break;
+        default: k_fwd_fused_df<MODE, 4><<<grid, kThreads, smem, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t fused_df_attributes(int bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k_fwd_fused_df<MODE, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_fused_df<MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_fused_df<MODE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_fused_df<MODE, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_fused_df<MODE, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
 // psi_0 = |j_b> (the tile is zeroed before): df64 one = (1, 0, 0, 0).
 __global__ void k_init_unit_df(float4 *psi0, const int32_t *cols, int B, int log2B, long long mask) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -917,7 +1064,16 @@ cudaError_t init_sweep_attributes_df64() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_bwd_dir_df2<kParity4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kDirDfSmem);
+    const int fmax = (int)fused_smem_bytes(kMaxWindow, kMaxDirs, kMaxPassGates, 1);
+    if (e == cudaSuccess) e = fused_df_attributes<kGeneral>(fmax);
+    if (e == cudaSuccess) e = fused_df_attributes<kParity4>(fmax);
     return e;
+}
+
+cudaError_t launch_fwd_fused_df64(const FwdFusedArgs &a, int grid, cudaStream_t s) {
+    const size_t smem = fused_smem_bytes(a.pass.q, a.kdirs, a.pass.m, 1);
+    return a.mode == kGeneral ? launch_fused_df_mode<kGeneral>(a, grid, smem, s)
+                              : launch_fused_df_mode<kParity4>(a, grid, smem, s);
 }
 
 void launch_init_unit_df64(double2 *psi0, const int32_t *cols, int B, int log2B, long long n_store,

@@ -24,8 +24,10 @@ EXPORTS = ("rq_create", "rq_destroy", "rq_setup_target", "rq_set_columns", "rq_s
            "rq_tr_step", "rq_target_column", "rq_get_info", "rq_profile_start", "rq_profile_stop",
            "rq_cost_static", "rq_set_gradient_space", "rq_batch_create", "rq_batch_destroy",
            "rq_batch_add", "rq_batch_set_tile", "rq_batch_hvp", "rq_batch_info", "rq_batch_last_error",
+           "rq_batch_set_fusion", "rq_batch_fusion_info",
            "rq_set_arithmetic", "rq_set_translation", "rq_hessian", "rq_set_checkpointing",
-           "rq_set_graphs", "rq_set_checks", "rq_set_first_layer", "rq_last_error")
+           "rq_set_graphs", "rq_set_checks", "rq_set_first_layer", "rq_set_fusion", "rq_fusion_info",
+           "rq_last_error")
 
 
 class RQCircuit(C.Structure):
@@ -102,6 +104,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "rq_set_graphs": ([vp, C.c_int], C.c_int),
         "rq_set_checks": ([vp, C.c_int], C.c_int),
         "rq_set_first_layer": ([vp, C.c_int], C.c_int),
+        "rq_set_fusion": ([vp, C.c_int], C.c_int),
+        "rq_fusion_info": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
         "rq_batch_create": ([C.POINTER(vp), C.c_int], C.c_int),
         "rq_batch_destroy": ([vp], C.c_int),
         "rq_batch_add": ([vp, C.POINTER(RQTarget), C.POINTER(RQCircuit), C.POINTER(C.c_int)], C.c_int),
@@ -109,6 +113,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "rq_batch_hvp": ([vp, dp, dp, C.c_int, C.c_int, dp, dp, dp], C.c_int),
         "rq_batch_info": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int), dp], C.c_int),
         "rq_batch_last_error": ([vp], C.c_char_p),
+        "rq_batch_set_fusion": ([vp, C.c_int], C.c_int),
+        "rq_batch_fusion_info": ([vp, C.POINTER(C.c_int), dp], C.c_int),
         "rq_profile_stop": ([vp, C.POINTER(RQKernelStat), C.c_int, C.POINTER(C.c_int)], C.c_int),
         "rq_last_error": ([vp], C.c_char_p),
     }
@@ -221,6 +227,15 @@ class Context:
     def set_first_layer(self, enable: bool):
         """Sweep only the nonzero items of the first layer's gates (default on)."""
         self._check(self._lib.rq_set_first_layer(self._h, 1 if enable else 0))
+
+    def set_fusion(self, max_window_qubits: int):
+        self._check(self._lib.rq_set_fusion(self._h, int(max_window_qubits)))
+        return self
+
+    def fusion_info(self) -> dict:
+        n, fg, mx = C.c_int(), C.c_int(), C.c_int()
+        self._check(self._lib.rq_fusion_info(self._h, C.byref(n), C.byref(fg), C.byref(mx)))
+        return {"passes": n.value, "fused_gates": fg.value, "max_pass_gates": mx.value}
 
     def set_checks(self, enable: bool):
         """Validate the gates of every call (unitarity, parity pattern)."""
@@ -395,8 +410,16 @@ class Batch:
         n, t = C.c_int(), C.c_int()
         ms = (C.c_double * 4)()
         self._check(self._lib.rq_batch_info(self._h, C.byref(n), C.byref(t), ms))
+        q = C.c_int()
+        fms = (C.c_double * 4)()
+        self._check(self._lib.rq_batch_fusion_info(self._h, C.byref(q), fms))
         return {"n_problems": n.value, "columns_per_tile": t.value,
-                "tune_ms": dict(zip((64, 128, 256, 512), list(ms)))}
+                "tune_ms": dict(zip((64, 128, 256, 512), list(ms))),
+                "fusion_window": q.value, "fusion_tune_ms": dict(zip((0, 4, 5, 6), list(fms)))}
+
+    def set_fusion(self, max_window_qubits: int):
+        """-1: autotune the fusion window at the next evaluation; 0: off; 3..6."""
+        self._check(self._lib.rq_batch_set_fusion(self._h, int(max_window_qubits)))
 
     def hvp(self, gates_list, dirs_list, plain: bool = False):
         """Per-problem lists in, per-problem (f, rgrad, hvps) lists out."""

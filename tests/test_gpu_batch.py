@@ -64,3 +64,32 @@ def test_batch_fixed_tile_and_new_gates(rq):
     assert not np.array_equal(f1, f2)
     for i in range(len(probs)):
         assert np.array_equal(h2[i], h3[i])
+
+
+def test_batch_fusion_window_autotuned_and_fixed(rq):
+    """The gates-per-pass autotuner times windows 0, 4, 5, 6 after the tile;
+    a fixed window gives batched == plain bit for bit and the oracle's values."""
+    probs = _problems()[:6]
+    gates = [p.gates for p in probs]
+    dirs = [w.random_directions(p.n_params, 1, 600 + i) for i, p in enumerate(probs)]
+    b = rq.Batch(0)
+    for p in probs:
+        b.add_problem(p)
+    f0, g0, h0 = b.hvp(gates, dirs)
+    info = b.info()
+    assert all(v > 0 for v in info["fusion_tune_ms"].values()), info
+    assert info["fusion_window"] in (0, 4, 5, 6)
+    b.set_fusion(6)
+    f1, g1, h1 = b.hvp(gates, dirs)
+    f2, g2, h2 = b.hvp(gates, dirs, plain=True)
+    assert b.info()["fusion_window"] == 6
+    assert np.array_equal(f1, f2)
+    for i, p in enumerate(probs):
+        assert np.array_equal(g1[i], g2[i]) and np.array_equal(h1[i], h2[i])
+        assert abs(f1[i] - f0[i]) <= 1e-13 * abs(f0[i])
+        assert_close(h1[i], h0[i], p.n, rtol=1e-13)
+        if p.n <= 8:
+            f, g, hv, _ = oracle_eval(p, range(1 << p.n), dirs[i], chunk=64)
+            assert abs(f1[i] - f) <= 1e-12 * abs(f)
+            assert_close(g1[i], g, p.n)
+            assert_close(h1[i], hv, p.n)

@@ -53,18 +53,23 @@ def test_n14_tile512(rq, arith):
 
 
 @pytest.mark.parametrize("arith", [0, 1])
-@pytest.mark.parametrize("structure,fname", [(0, "tile16_general.json"), (1, "tile16_parity.json")])
-def test_n16_benchmark_tile(rq, arith, structure, fname):
-    """The benchmark's own configuration: automatic tile choice (512 columns,
-    one direction per sweep), its first step's columns."""
+@pytest.mark.parametrize("structure,fname,tile,B,n_tiles", [
+    (0, "tile16_general.json", 0, 512, 1),   # the benchmark: automatic choice, one 512-column tile
+    (1, "tile16_parity.json", 0, 256, 4),    # parity, automatic choice: 256-column tiles (as benchmarked)
+    (1, "tile16_parity.json", 512, 512, 2),  # parity: an even and an odd 512-column tile
+])
+def test_n16_benchmark_tile(rq, arith, structure, fname, tile, B, n_tiles):
+    """The benchmark instance in the benchmark's launch configuration (its
+    automatic tile choice) and one more tile size, its first columns."""
     gold = load_golden(fname)
     prob = w.config_problem("n16", structure=structure)
     X = w.random_directions(prob.n_params, 1, gold["direction_seed"])
     with rq.Context(0) as ctx:
         ctx.setup_problem(prob)
         ctx.set_arithmetic(arith)
+        if tile:
+            ctx.set_tile(tile, 1)
         ctx.set_columns(*gold["columns"])
         info = ctx.info()
-        assert info["columns_per_tile"] == 512 and info["max_dirs"] == 1
-        assert info["n_tiles"] == (1 if structure == 0 else 2)
-        _check(ctx.hvp(prob.gates, X), gold, prob.n, f"n16 structure {structure} arith {arith}")
+        assert info["columns_per_tile"] == B and info["n_tiles"] == n_tiles, info
+        _check(ctx.hvp(prob.gates, X), gold, prob.n, f"n16 structure {structure} tile {B} arith {arith}")
