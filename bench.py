@@ -74,6 +74,13 @@ WORKLOAD = ("spinful Fermi-Hubbard chain, 8 sites (n=16 qubits), open, J=1 U=4 t
             "f + Riemannian grad + 1 Riemannian HVP (direction seed 1602) summed over all 65536 basis columns")
 
 
+def bench_config(world: int) -> dict:
+    """The workload description both arms print (identical dicts)."""
+    return {"workload": WORKLOAD, "structure": "general", "hvp_directions": 1,
+            "l2": "inputs larger than L2 (each tile state is 512 MiB)",
+            "parallelism": f"column shards x{world}" if world > 1 else "single GPU"}
+
+
 def _measured_hbm():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -216,16 +223,17 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     import workloads as w
-    from paper_2506_23775_gb300 import rq
+    from paper_2506_23775_gb300 import rq, shard
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)   # the library runs on this stream; events are recorded on it
 
-    def measure(structure: int, steps: int, warmup: int, tile: int, arith: int = 0):
+    def measure(structure: int, steps: int, warmup: int, tile: int, arith: int = 0, fuse: int = 0):
         prob = make_workload(args, structure)
         X = w.random_directions(prob.n_params, 1, 1602)
         ctx = rq.Context(local, stream=stream.cuda_stream).setup_problem(prob)
         ctx.set_arithmetic(arith)
+        ctx.set_fusion(fuse)
         if tile:
             ctx.set_tile(tile, 1)
         ncols = 1 << prob.n
@@ -237,14 +245,22 @@ def run_ours(args):
         f_t = torch.zeros(1, dtype=torch.float64, device=dev)
         rg_t = torch.zeros_like(gates)
         hv_t = torch.zeros_like(dirs)
+        ds = shard.DeviceShard(ctx, prob.n_params, 1, dev) if world > 1 else None
 
         def batch_range(s):
-            c0 = ((rank * (steps + warmup) + s) * batch) % ncols
+            # step s covers world consecutive batches; rank r takes the r-th
+            c0 = ((s * world + rank) * batch) % ncols
             return c0, min(c0 + batch, ncols)
 
         def step(s):
             ctx.set_columns(*batch_range(s))
-            ctx.hvp_dev(gates.data_ptr(), dirs.data_ptr(), 1, f_t.data_ptr(), rg_t.data_ptr(), hv_t.data_ptr())
+            if ds is None:
+                ctx.hvp_dev(gates.data_ptr(), dirs.data_ptr(), 1, f_t.data_ptr(), rg_t.data_ptr(), hv_t.data_ptr())
+            else:
+                # this rank's partial straight into the gathered buffer, then
+                # the all-gather and the rank-order sum (inside the timed region)
+                ds.evaluate(gates.data_ptr(), dirs.data_ptr())
+                ds.total(stream=stream)
 
         for s in range(warmup):
             step(s)
@@ -287,7 +303,10 @@ def run_ours(args):
         t0 = time.perf_counter()
         for s in range(e2e_steps):
             ctx.set_columns(*batch_range(s))
-            ctx.hvp(g_h, d_h, out=(rg_h, hv_h))
+            res = ctx.hvp(g_h, d_h, out=(rg_h, hv_h))
+            if world > 1:   # the public sharded path: partials exchanged, summed in rank order
+                part = torch.from_numpy(shard.pack(*res)).to(dev)
+                shard.exchange(part)
         e2e_s = time.perf_counter() - t0
         tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
         if world > 1:
@@ -296,6 +315,7 @@ def run_ours(args):
                "h2d_bytes_per_step": int(g_h.nbytes + d_h.nbytes),
                "d2h_bytes_per_step": int(8 + rg_h.nbytes + hv_h.nbytes)}
         info = ctx.info()
+        info["fusion"] = ctx.fusion_info()
         ctx.close()
         return dict(value=value, ms_per_step=ms_max / steps, ms_per_step_median=statistics.median(step_ms),
                     launches=launches, prof=prof, clocks=clk.summary(),
@@ -316,18 +336,23 @@ def run_ours(args):
         t0 = time.perf_counter()
         b.hvp(gates, dirs)                      # autotune + capture + first replay
         first_s = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        fb, _, _ = b.hvp(gates, dirs)
-        batched_s = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        fp, _, _ = b.hvp(gates, dirs, plain=True)
-        plain_s = time.perf_counter() - t0
+        tb, tp = [], []
+        for _ in range(args.repeats):          # alternating, so drifts hit both alike
+            t0 = time.perf_counter()
+            fb, _, _ = b.hvp(gates, dirs)
+            tb.append(time.perf_counter() - t0)
+            t0 = time.perf_counter()
+            fp, _, _ = b.hvp(gates, dirs, plain=True)
+            tp.append(time.perf_counter() - t0)
+        batched_s, plain_s = statistics.median(tb), statistics.median(tp)
         info = b.info()
         b.close()
         flops = sum(9 * p.n_gates * 32.0 * 4 ** p.n for p in probs)
         return {"problems": len(probs), "unit": "problem evals/s",
                 "batched": len(probs) / batched_s, "plain": len(probs) / plain_s,
                 "speedup": plain_s / batched_s, "batched_s": batched_s, "plain_s": plain_s,
+                "repeats": args.repeats, "batched_s_all": tb, "plain_s_all": tp,
+                "timing": "median of the repeats, wall clock of the synchronous host call",
                 "bitwise_equal": bool(np.array_equal(fb, fp)), "columns_per_tile": info["columns_per_tile"],
                 "autotune_ms": info["tune_ms"], "setup_s": setup_s, "first_call_s": first_s,
                 "fp64_tflops_batched": flops / batched_s / 1e12,
@@ -455,6 +480,159 @@ def run_ours(args):
                 "vs_layers_10_qubits": [point(5, d) for d in (1, 3, 5, 7, 9, 11, 15, 21)],
                 "shapes": [point(5, 11), point(6, 3), point(8, 11)]}
 
+    def measure_fusion(steps: int = 4):
+        """Window fusion of the forward pass (rq_set_fusion, windows of 6 stored
+        qubits) against the unfused schedule at the benchmark instance: the
+        f + grad + 1 HVP step of the headline (FP64 and double-float, general
+        and parity gates) and a cost-only evaluation, where fusion also drops
+        the intermediate states' HBM writes.  Events on the library stream,
+        per-family device time from the library's profiling."""
+        out = {"window_qubits": 6}
+        for arith, aname in ((0, "fp64"), (1, "df64")):
+            for structure, sname in ((0, "general"), (1, "parity")):
+                res = {}
+                for fuse in (0, 6):
+                    r = measure(structure, steps, 3, args.tile, arith=arith, fuse=fuse)
+                    fam = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                               "gbs": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1),
+                               "bytes_per_eval": v["bytes"] * (1 << N_QUBITS) / (steps * r["batch"])}
+                           for k, v in r["prof"].items() if k == "fwd_gate"}
+                    res["fused" if fuse else "unfused"] = {"value": r["value"], "ms_per_step": r["ms_per_step"],
+                                                           "fwd": fam.get("fwd_gate"), "plan": r["info"]["fusion"]}
+                res["speedup"] = res["fused"]["value"] / res["unfused"]["value"]
+                out[f"{aname}_{sname}"] = res
+            # cost only (no checkpoints kept): general gates, one 512-column tile
+            prob = make_workload(args, 0)
+            cres = {}
+            for fuse in (0, 6):
+                ctx = rq.Context(local, stream=stream.cuda_stream).setup_problem(prob)
+                ctx.set_arithmetic(arith)
+                ctx.set_fusion(fuse)
+                ctx.set_columns(0, 512)
+                g_d = torch.from_numpy(prob.gates.copy()).to(dev)
+                f_d = torch.zeros(1, dtype=torch.float64, device=dev)
+                ctx.cost_dev(g_d.data_ptr(), f_d.data_ptr())
+                torch.cuda.synchronize()
+                ctx.profile_start()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for s_ in range(steps):
+                    c0 = ((s_ + 1) * 512) % (1 << prob.n)
+                    ctx.set_columns(c0, c0 + 512)
+                    ctx.cost_dev(g_d.data_ptr(), f_d.data_ptr())
+                e1.record(stream)
+                torch.cuda.synchronize()
+                prof = ctx.profile_stop()
+                ms = e0.elapsed_time(e1) / steps
+                fw = prof.get("fwd_gate", {"bytes": 0.0, "ms": 1.0})
+                cres["fused" if fuse else "unfused"] = {
+                    "ms_per_tile": ms, "evals_per_s": 512 / (1 << prob.n) / (ms * 1e-3),
+                    "fwd_bytes_per_eval": fw["bytes"] * (1 << prob.n) / (steps * 512),
+                    "fwd_gbs": fw["bytes"] / max(fw["ms"], 1e-9) / 1e6, "plan": ctx.fusion_info()}
+                ctx.close()
+            cres["speedup"] = cres["unfused"]["ms_per_tile"] / cres["fused"]["ms_per_tile"]
+            out[f"{aname}_cost"] = cres
+        return out
+
+    def measure_strong(total_cols: int = 4096, reps: int = 3):
+        """Strong scaling: a fixed workload of ``total_cols`` basis columns of
+        the benchmark instance (general gates, FP64, f + grad + 1 HVP) split
+        into one contiguous shard per rank, partials exchanged and summed in
+        rank order, every repeat timed with CUDA events (max over ranks)."""
+        prob = make_workload(args, 0)
+        X = w.random_directions(prob.n_params, 1, 1602)
+        ctx = rq.Context(local, stream=stream.cuda_stream).setup_problem(prob)
+        c0, c1 = shard.column_shard(total_cols, rank, world)
+        ctx.set_columns(c0, c1)
+        gates = torch.from_numpy(prob.gates.copy()).to(dev)
+        dirs = torch.from_numpy(X.copy()).to(dev)
+        ds = shard.DeviceShard(ctx, prob.n_params, 1, dev)
+
+        def once():
+            ds.evaluate(gates.data_ptr(), dirs.data_ptr())
+            if world > 1:
+                ds.total(stream=stream)
+        once()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            once()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = torch.tensor([e0.elapsed_time(e1) / reps], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        ctx.close()
+        return {"columns": total_cols, "ranks": world, "columns_per_rank": c1 - c0, "repeats": reps,
+                "ms": ms, "value": total_cols / (1 << prob.n) / (ms * 1e-3), "unit": UNIT,
+                "note": "fixed total work split over the ranks (strong scaling), exchange included"}
+
+    def measure_full():
+        """One whole evaluation: f + grad + 1 HVP over all 65536 columns of
+        the benchmark instance through the host C-ABI call rq_hvp (general
+        gates, FP64, direct launches), timed once with CUDA events on the
+        context stream and with the host clock."""
+        prob = make_workload(args, 0)
+        X = w.random_directions(prob.n_params, 1, 1602)
+        ctx = rq.Context(local, stream=stream.cuda_stream).setup_problem(prob)
+        ctx.set_graphs(False)          # 128 tiles: no need to capture a 70k-node graph
+        ctx.set_columns(0, 1 << prob.n)
+        g_h = torch.from_numpy(prob.gates.copy()).pin_memory().numpy()
+        d_h = torch.from_numpy(X.copy()).pin_memory().numpy()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            e0.record(stream)
+            f, g, hv = ctx.hvp(g_h, d_h)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        ms = e0.elapsed_time(e1)
+        info = ctx.info()
+        ctx.close()
+        return {"columns": 1 << prob.n, "tiles": info["n_tiles"], "s_event": ms * 1e-3, "s_wall": wall,
+                "evals_per_s": 1.0 / (ms * 1e-3), "unit": UNIT, "f": f, "clocks": clk.summary(),
+                "grad_norm": float(np.linalg.norm(g)), "hvp_norm": float(np.linalg.norm(hv))}
+
+    def measure_pipes():
+        """Measured FMA throughput of the FP64 and FP32 pipes (libpeak.so)."""
+        import ctypes
+        lib = ctypes.CDLL(_build.PEAK_LIB)
+        out = {}
+        for name in ("fp64", "fp32"):
+            fn = getattr(lib, f"pp_{name}_fma_rate")
+            fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+            tf, ms = ctypes.c_double(), ctypes.c_double()
+            with ClockSampler(local) as clk:
+                rc = fn(local, 5, ctypes.byref(tf), ctypes.byref(ms))
+            out[name] = {"tflops": tf.value if rc == 0 else None, "ms_per_launch": ms.value, "rc": rc,
+                         "clocks": clk.summary()}
+        out["how"] = ("8 independent FMA chains per thread, 2 CTAs of 256 threads per SM, CUDA events over "
+                      "5 launches after a warm-up; 2 flops per FMA")
+        return out
+
+    if args.cost_only:     # profiling cases only: cost evaluations with or without fusion
+        prob = make_workload(args, 0)
+        ctx = rq.Context(local, stream=stream.cuda_stream).setup_problem(prob)
+        ctx.set_arithmetic(1 if args.df64_only else 0)
+        ctx.set_fusion(args.fusion)
+        B = min(512, 1 << prob.n)
+        ctx.set_tile(B, 1)
+        g_d = torch.from_numpy(prob.gates.copy()).to(dev)
+        f_d = torch.zeros(1, dtype=torch.float64, device=dev)
+        for s_ in range(args.warmup + args.steps):
+            c0 = (s_ * B) % (1 << prob.n)
+            ctx.set_columns(c0, c0 + B)
+            ctx.cost_dev(g_d.data_ptr(), f_d.data_ptr())
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": "cost only (profiling)", "n": prob.n, "gates": prob.n_gates, "fusion": args.fusion,
+                          "plan": ctx.fusion_info(), "columns_per_tile": B, "f_last_tile": float(f_d.item())}))
+        return
     if args.parity_only:   # profiling cases only: the parity-gate sweep alone
         par = measure(1, args.steps, args.warmup, args.tile)
         if rank == 0:
@@ -475,6 +653,10 @@ def run_ours(args):
     served = measure_served() if (not args.no_served and world == 1) else None
     sweeps = measure_sweeps() if (args.sweeps and world == 1) else None
     kind_rates = measure_rates() if (not args.general_only and world == 1) else None
+    fusion = measure_fusion() if (not args.no_fusion and world == 1) else None
+    strong = measure_strong() if not args.no_strong else None
+    full = measure_full() if (not args.no_full and world == 1) else None
+    pipes = measure_pipes() if world == 1 else None
 
     if rank != 0:
         if world > 1:
@@ -499,8 +681,11 @@ def run_ours(args):
             # FP32-pipe operations: 12 per real product term, 4 terms per complex
             # multiply-add of 8 FP64-equivalent flops (normalisations not counted)
             ops = d["flops"] * 6.0 / (d["ms"] * 1e-3) / 1e12
+            meas32 = pipes["fp32"]["tflops"] / 2.0 if pipes and pipes["fp32"]["tflops"] else None  # FMAs/s
             return {"kernel": dom, "bound": "alu", "achieved": round(ops, 3), "peak": round(FP32_PIPE_TOPS, 3),
                     "unit": "Tops/s (FP32 pipe)", "frac": round(ops / FP32_PIPE_TOPS, 4), "traffic": None,
+                    "peak_measured": round(meas32, 3) if meas32 else None,
+                    "frac_of_measured": round(ops / meas32, 4) if meas32 else None,
                     "peak_source": "derived: 128 FP32 lanes x 152 SMs x 2.07 GHz",
                     "fp64_equivalent_tflops": round(achieved, 4), "launch_ms": round(per_launch_ms, 4),
                     "hbm_achieved_gbs": round(d["bytes"] / (d["ms"] * 1e-3) / 1e9, 1),
@@ -514,8 +699,12 @@ def run_ours(args):
                    "share": round(v["ms"] / sum(x["ms"] for x in res["prof"].values()), 4),
                    "tflops": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 4),
                    "gbs": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)} for k, v in res["prof"].items()}
+        meas = pipes["fp64"]["tflops"] if pipes else None
         return {"kernel": dom, "bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                "peak_measured": round(meas, 4) if meas else None,
+                "frac_of_measured": round(achieved / meas, 4) if meas else None,
+                "peak_measured_source": "FP64 FMA-chain probe (libpeak.so) in this run" if meas else None,
                 "traffic_note": traffic_note,
                 "flop_convention": "4 real multiply-adds per complex multiply-add (8 flops)",
                 "fp64_pipe_frac": round(achieved * (PIPE_PER_FLOP_GENERAL.get(dom, 1.0) if general else 1.0)
@@ -532,10 +721,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": gen["ms_per_step"], "ms_per_step_median": gen["ms_per_step_median"],
         "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "structure": "general", "columns_per_step": gen["batch"],
-                   "columns_per_tile": gen["B"], "hvp_directions": 1,
-                   "l2": "inputs larger than L2 (each tile state is 512 MiB)",
-                   "parallelism": f"column shards x{world}" if world > 1 else "single GPU"},
+        "config": bench_config(world), "columns_per_step": gen["batch"] * world, "columns_per_rank_step": gen["batch"],
+        "columns_per_tile": gen["B"],
         "roofline": roofline(gen, headline=True, general=True), "e2e": gen["e2e"], "gpu_launches": gen["launches"], "clocks": gen["clocks"],
     }
     if par is not None:
@@ -560,6 +747,14 @@ def run_ours(args):
         line["sweeps"] = sweeps
     if kind_rates is not None:
         line["rates"] = kind_rates
+    if fusion is not None:
+        line["fusion"] = fusion
+    if strong is not None:
+        line["strong"] = strong
+    if full is not None:
+        line["full_eval"] = full
+    if pipes is not None:
+        line["pipes_measured"] = pipes
     if world == 1 and not args.no_cpu:
         rates, cores, ncols = cpu_oracle_rate(per_worker=1, repeats=2)   # first round warms up
         line["cpu_baseline"] = {"value": rates[-1], "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -593,7 +788,7 @@ def run_reference(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD, "structure": "general", "columns_per_step": cores},
+        "config": bench_config(int(os.environ.get("WORLD_SIZE", "1"))), "columns_per_step": cores,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"each step: {cores} basis columns of the (4,4) sector, one per spawned "
                                    "process (numpy oracle, the paper's matrix-free algorithm)"},
@@ -617,6 +812,13 @@ def main():
     ap.add_argument("--sweeps", action="store_true", help="also time the gradient per summand vs n and layers")
     ap.add_argument("--no-df64", action="store_true", help="skip the double-float arithmetic measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-strong", action="store_true", help="skip the strong-scaling measurement")
+    ap.add_argument("--no-fusion", action="store_true", help="skip the fused-vs-unfused forward measurement")
+    ap.add_argument("--no-full", action="store_true", help="skip the whole 65536-column evaluation")
+    ap.add_argument("--repeats", type=int, default=5, help="repeats of the batched-vs-plain comparison (median)")
+    ap.add_argument("--cost-only", action="store_true", help="run cost evaluations only (profiling cases only)")
+    ap.add_argument("--df64-only", action="store_true", help="with --cost-only: double-float arithmetic")
+    ap.add_argument("--fusion", type=int, default=0, help="with --cost-only: fusion window (0 = off)")
     ap.add_argument("--sites", type=int, default=8, help="chain sites (n = 2 * sites); profiling cases only")
     ap.add_argument("--depth", type=int, default=11, help="brickwall layers; profiling cases only")
     args = ap.parse_args()
