@@ -22,7 +22,7 @@ LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "librq.so")
 PEAK_LIB = os.path.join(LIBDIR, "libpeak.so")
 PEAK_SOURCE = "peak_probe.cu"
-SOURCES = ["rq_api.cu", "rq_sweep.cu", "rq_target.cu", "rq_geometry.cu", "rq_tr.cpp", "rq_static.cu", "rq_batch.cu", "rq_sweep_df64.cu", "rq_hessian.cu"]
+SOURCES = ["rq_context.cu", "rq_setup.cu", "rq_eval.cu", "rq_sweep.cu", "rq_target.cu", "rq_geometry.cu", "rq_tr.cpp", "rq_static.cu", "rq_batch.cu", "rq_sweep_df64.cu", "rq_hessian.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(ROOT, "include")]
 

@@ -106,6 +106,7 @@ struct FwdFusedArgs {
     int log2chunks;             // log2(B / 32)
     long long n_blocks;         // (n_store >> q) << log2chunks
     long long outer_mask;       // stored bits outside the window
+    int nbuf;                   // 2: copy the next block in while the current one is computed; 1: not
     FusedPass pass;
 };
 
@@ -127,9 +128,11 @@ void launch_bwd_base(const BwdArgs &a, int grid, cudaStream_t s);
 void launch_bwd_dir(const BwdArgs &a, int grid, cudaStream_t s);
 void launch_init_unit(double2 *psi0, const int32_t *cols, int B, int log2B, long long n_store,
                       int parity_layout, cudaStream_t s);
-// Fused forward pass (shared-memory bytes of the launch from fused_smem_bytes).
-size_t fused_smem_bytes(int q, int kdirs, int m, int df64);
-cudaError_t launch_fwd_fused(const FwdFusedArgs &a, int grid, cudaStream_t s);
+// Fused forward pass: shared-memory bytes of a launch with nbuf block sets
+// (the same for FP64 and double-float), and the most any launch may use.
+constexpr size_t kMaxFusedSmem = 227 * 1024;
+size_t fused_smem_bytes(int q, int kdirs, int m, int nbuf);
+cudaError_t launch_fwd_fused(const FwdFusedArgs &a, int sms, cudaStream_t s);
 
 // Launchers (rq_sweep_df64.cu): the same steps in double-float arithmetic;
 // tiles, gates and directions hold float4 (hi, lo, hi, lo) in the same bytes.
@@ -138,7 +141,7 @@ void launch_bwd_base_df64(const BwdArgs &a, int grid, cudaStream_t s);
 void launch_bwd_dir_df64(const BwdArgs &a, int grid, cudaStream_t s);
 void launch_init_unit_df64(double2 *psi0, const int32_t *cols, int B, int log2B, long long n_store, cudaStream_t s);
 void launch_to_df64(const double2 *in, double2 *out, long long n, cudaStream_t s);
-cudaError_t launch_fwd_fused_df64(const FwdFusedArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_fwd_fused_df64(const FwdFusedArgs &a, int sms, cudaStream_t s);
 void launch_scatter_target_df64(const TargetDev &t, const int32_t *cols, const double *wts, int B, int log2B,
                                 int parity_layout, int n, double2 *lam, const double2 *psi_final, double *fpart,
                                 cudaStream_t s);
@@ -172,7 +175,7 @@ void launch_geometry(const double2 *gates, const double2 *dirs, const double *en
                      int k, int structure, int euclidean, const double *facc, double *f_out, double2 *rgrad,
                      double2 *hvps, cudaStream_t s);
 
-// Host-memory evaluation (rq_api.cu): copies inputs in and outputs out and
+// Host-memory evaluation (rq_eval.cu): copies inputs in and outputs out and
 // synchronises.  want_env: 0 no gradient environments, 1 accumulate them,
 // 2 reuse those of the previous evaluation at the same gates (HVPs need them
 // for the Riemannian correction).
@@ -190,7 +193,7 @@ rq_status prepare_capacity(rq_ctx *ctx, int k);
 cudaStream_t ctx_stream(const rq_ctx *ctx);
 long long workspace_bytes_for(const rq_ctx *ctx, int columns_per_tile, int kc);
 
-// Read-only view of a set-up context for entry points outside rq_api.cu.
+// Read-only view of a set-up context for entry points outside the context files.
 struct CtxView {
     bool ready;
     int device, n, g, P, structure, sms;

@@ -54,6 +54,8 @@
 // direction).
 #include "rq_items.cuh"
 
+#include <algorithm>
+
 namespace rq {
 namespace {
 
@@ -681,11 +683,12 @@ __global__ void __launch_bounds__(kThreads, MODE == kGeneral ? 1 : 2) k_bwd_dir(
 // their tangent steps) there, and writes a gate's output to HBM only where a
 // checkpoint slot is wanted (every gate when the backward pass needs the
 // states, the last one otherwise).  Same arithmetic per item as k_fwd.
-// Shared memory: (1 + KD) state blocks, the gates' tables, a row -> stored
-// offset table.
+// Shared memory: nbuf sets of (1 + KD) state blocks, the gates' tables, a
+// row -> stored offset table.  With two sets the next block's amplitudes are
+// copied in (cp.async) while the current block's gates run.
 
-size_t fused_bytes(int q, int kd, int m) {
-    return (size_t)(1 + kd) * ((size_t)32 << q) * sizeof(double2) + (size_t)(1 + kd) * m * sizeof(Mat3) +
+size_t fused_bytes(int q, int kd, int m, int nbuf) {
+    return (size_t)nbuf * (1 + kd) * ((size_t)32 << q) * sizeof(double2) + (size_t)(1 + kd) * m * sizeof(Mat3) +
            ((size_t)1 << q) * sizeof(long long);
 }
 
@@ -695,10 +698,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_fwd_fused(const FwdFusedArgs a)
     const FusedPass &p = a.pass;
     const int rows = 1 << p.q, m = p.m;
     const int elems = rows * 32, items = (rows >> 2) * 32;
-    double2 *S = reinterpret_cast<double2 *>(fused_raw);             // [1 + KD][rows][32]
-    Mat3 *mg = reinterpret_cast<Mat3 *>(S + (1 + KD) * elems);       // [m]
-    Mat3 *mx = mg + m;                                                // [KD][m]
-    long long *rowoff = reinterpret_cast<long long *>(mx + KD * m);  // [rows]
+    double2 *const Sb = reinterpret_cast<double2 *>(fused_raw);           // [nbuf][1 + KD][rows][32]
+    Mat3 *mg = reinterpret_cast<Mat3 *>(Sb + a.nbuf * (1 + KD) * elems);  // [m]
+    Mat3 *mx = mg + m;                                                     // [KD][m]
+    long long *rowoff = reinterpret_cast<long long *>(mx + KD * m);       // [rows]
     for (int e = threadIdx.x; e < m * 16; e += blockDim.x) {
         const int j = e >> 4;
         tabulate3(mg[j], a.gates + (long long)p.param[j] * 16, e & 15, 0);
@@ -709,16 +712,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_fwd_fused(const FwdFusedArgs a)
     for (int r = threadIdx.x; r < rows; r += blockDim.x) rowoff[r] = deposit_bits(r, p.wmask);
     __syncthreads();
     const long long cmask = (1LL << a.log2chunks) - 1;
-    for (long long blk = blockIdx.x; blk < a.n_blocks; blk += gridDim.x) {
+    auto load = [&](long long blk, double2 *dst) {
         const long long x0 = deposit_bits(blk >> a.log2chunks, a.outer_mask);
         const long long col0 = (blk & cmask) << 5;
         for (int e = threadIdx.x; e < elems; e += blockDim.x) {
             const long long off = ((x0 | rowoff[e >> 5]) << a.log2B) | (col0 + (e & 31));
-            S[e] = __ldg(&a.psi_in[off]);
+            cp_async16(dst + e, a.psi_in + off);
 #pragma unroll
-            for (int d = 0; d < KD; ++d) S[(1 + d) * elems + e] = __ldg(&a.dpsi_in[d * a.dir_stride + off]);
+            for (int d = 0; d < KD; ++d) cp_async16(dst + (1 + d) * elems + e, a.dpsi_in + d * a.dir_stride + off);
+        }
+    };
+    long long blk = blockIdx.x;
+    if (blk < a.n_blocks) load(blk, Sb);
+    cp_async_commit();
+    int cur = 0;
+    for (; blk < a.n_blocks; blk += gridDim.x) {
+        const long long nxt = blk + gridDim.x;
+        if (a.nbuf == 2) {
+            if (nxt < a.n_blocks) load(nxt, Sb + (cur ^ 1) * (1 + KD) * elems);
+            cp_async_commit();
+            cp_async_wait<1>();  // this block's copies have landed
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
+        double2 *S = Sb + cur * (1 + KD) * elems;
+        const long long x0 = deposit_bits(blk >> a.log2chunks, a.outer_mask);
+        const long long col0 = (blk & cmask) << 5;
         for (int j = 0; j < m; ++j) {
             const int la = p.la[j], lb = p.lb[j];
             const int lo = la < lb ? la : lb, hi = la < lb ? lb : la;
@@ -758,21 +778,39 @@ __global__ void __launch_bounds__(kThreads, 1) k_fwd_fused(const FwdFusedArgs a)
                     }
                 }
             }
-            __syncthreads();
+            __syncthreads();  // the next gate (or the next block's copies) may overwrite S
+        }
+        if (a.nbuf == 2) {
+            cur ^= 1;
+        } else {
+            if (nxt < a.n_blocks) load(nxt, Sb);
+            cp_async_commit();
         }
     }
+    cp_async_wait<0>();
+}
+
+// Grid: as many CTAs as fit on every SM at this shared-memory size (blocks
+// are dealt grid-stride), never more than there are blocks.
+template <class K>
+cudaError_t launch_resident(K kernel, const FwdFusedArgs &a, int sms, size_t smem, cudaStream_t s) {
+    int per_sm = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    const long long grid = std::min<long long>(a.n_blocks, (long long)sms * std::max(per_sm, 1));
+    kernel<<<(unsigned)grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <int MODE>
-cudaError_t launch_fused_mode(const FwdFusedArgs &a, int grid, size_t smem, cudaStream_t s) {
+cudaError_t launch_fused_mode(const FwdFusedArgs &a, int sms, size_t smem, cudaStream_t s) {
     switch (a.kdirs) {
-        case 0: k_fwd_fused<MODE, 0><<<grid, kThreads, smem, s>>>(a); break;
-        case 1: k_fwd_fused<MODE, 1><<<grid, kThreads, smem, s>>>(a); break;
-        case 2: k_fwd_fused<MODE, 2><<<grid, kThreads, smem, s>>>(a); break;
-        case 3: k_fwd_fused<MODE, 3><<<grid, kThreads, smem, s>>>(a); break;
-        default: k_fwd_fused<MODE, 4><<<grid, kThreads, smem, s>>>(a); break;
+        case 0: return launch_resident(k_fwd_fused<MODE, 0>, a, sms, smem, s);
+        case 1: return launch_resident(k_fwd_fused<MODE, 1>, a, sms, smem, s);
+        case 2: return launch_resident(k_fwd_fused<MODE, 2>, a, sms, smem, s);
+        case 3: return launch_resident(k_fwd_fused<MODE, 3>, a, sms, smem, s);
+        default: return launch_resident(k_fwd_fused<MODE, 4>, a, sms, smem, s);
     }
-    return cudaGetLastError();
 }
 
 template <int MODE>
@@ -821,15 +859,15 @@ void launch_bwd_dir(const BwdArgs &a, int grid, cudaStream_t s) {
     }
 }
 
-size_t fused_smem_bytes(int q, int kdirs, int m, int df64) {
-    (void)df64;  // double-float blocks and tables take the same bytes (float4 amplitudes, float2 triples)
-    return fused_bytes(q, kdirs, m);
+size_t fused_smem_bytes(int q, int kdirs, int m, int nbuf) {
+    // double-float blocks and tables take the same bytes (float4 amplitudes, float2 triples)
+    return fused_bytes(q, kdirs, m, nbuf);
 }
 
-cudaError_t launch_fwd_fused(const FwdFusedArgs &a, int grid, cudaStream_t s) {
-    const size_t smem = fused_bytes(a.pass.q, a.kdirs, a.pass.m);
-    return a.mode == kGeneral ? launch_fused_mode<kGeneral>(a, grid, smem, s)
-                              : launch_fused_mode<kParity4>(a, grid, smem, s);
+cudaError_t launch_fwd_fused(const FwdFusedArgs &a, int sms, cudaStream_t s) {
+    const size_t smem = fused_bytes(a.pass.q, a.kdirs, a.pass.m, a.nbuf);
+    return a.mode == kGeneral ? launch_fused_mode<kGeneral>(a, sms, smem, s)
+                              : launch_fused_mode<kParity4>(a, sms, smem, s);
 }
 
 cudaError_t init_sweep_attributes() {
@@ -842,7 +880,7 @@ cudaError_t init_sweep_attributes() {
         e = cudaFuncSetAttribute(k_bwd_base<kGeneral>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBaseSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_bwd_base<kParity4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBaseSmem);
-    const int fmax = (int)fused_bytes(kMaxWindow, kMaxDirs, kMaxPassGates);
+    const int fmax = (int)kMaxFusedSmem;
     if (e == cudaSuccess) e = fused_attributes<kGeneral>(fmax);
     if (e == cudaSuccess) e = fused_attributes<kParity4>(fmax);
     return e;

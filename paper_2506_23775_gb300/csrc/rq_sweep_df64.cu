@@ -25,6 +25,8 @@
 // compiler can neither contract nor reassociate the error-free transforms.
 #include "rq_items.cuh"
 
+#include <algorithm>
+
 namespace rq {
 namespace {
 
@@ -861,13 +863,13 @@ constexpr int kTabBytes = 384;
 static_assert(sizeof(MatDf3) <= kTabBytes && 16 * sizeof(float4) <= kTabBytes, "gate table size");
 
 template <int MODE, int KD>
-__global__ void __launch_bounds__(kThreads, 1) k_fwd_fused_df(const FwdFusedArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_fwd_fused_df(const FwdFusedArgs a) {
     extern __shared__ __align__(16) unsigned char fused_raw[];
     const FusedPass &p = a.pass;
     const int rows = 1 << p.q, m = p.m;
     const int elems = rows * 32, items = (rows >> 2) * 32;
-    float4 *S = reinterpret_cast<float4 *>(fused_raw);                      // [1 + KD][rows][32]
-    unsigned char *tab = reinterpret_cast<unsigned char *>(S + (1 + KD) * elems);  // [(1 + KD) m][kTabBytes]
+    float4 *const Sb = reinterpret_cast<float4 *>(fused_raw);                            // [nbuf][1 + KD][rows][32]
+    unsigned char *tab = reinterpret_cast<unsigned char *>(Sb + a.nbuf * (1 + KD) * elems);  // [(1 + KD) m][kTabBytes]
     long long *rowoff = reinterpret_cast<long long *>(tab + (size_t)(1 + KD) * m * kTabBytes);
     const float4 *gates = reinterpret_cast<const float4 *>(a.gates);
     const float4 *dirs = reinterpret_cast<const float4 *>(a.dirs);
@@ -891,16 +893,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_fwd_fused_df(const FwdFusedArgs
     float4 *psi_base = reinterpret_cast<float4 *>(a.psi_base);
     float4 *dpsi_base = reinterpret_cast<float4 *>(a.dpsi_base);
     const long long cmask = (1LL << a.log2chunks) - 1;
-    for (long long blk = blockIdx.x; blk < a.n_blocks; blk += gridDim.x) {
+    auto load = [&](long long blk, float4 *dst) {
         const long long x0 = deposit_bits(blk >> a.log2chunks, a.outer_mask);
         const long long col0 = (blk & cmask) << 5;
         for (int e = threadIdx.x; e < elems; e += blockDim.x) {
             const long long off = ((x0 | rowoff[e >> 5]) << a.log2B) | (col0 + (e & 31));
-            S[e] = __ldg(&psi_in[off]);
+            cp_async16_f4(dst + e, psi_in + off);
 #pragma unroll
-            for (int d = 0; d < KD; ++d) S[(1 + d) * elems + e] = __ldg(&dpsi_in[d * a.dir_stride + off]);
+            for (int d = 0; d < KD; ++d) cp_async16_f4(dst + (1 + d) * elems + e, dpsi_in + d * a.dir_stride + off);
+        }
+    };
+    long long blk = blockIdx.x;
+    if (blk < a.n_blocks) load(blk, Sb);
+    cp_async_commit_df();
+    int cur = 0;
+    for (; blk < a.n_blocks; blk += gridDim.x) {
+        const long long nxt = blk + gridDim.x;
+        if (a.nbuf == 2) {
+            if (nxt < a.n_blocks) load(nxt, Sb + (cur ^ 1) * (1 + KD) * elems);
+            cp_async_commit_df();
+            cp_async_wait_df<1>();  // this block's copies have landed
+        } else {
+            cp_async_wait_df<0>();
         }
         __syncthreads();
+        float4 *S = Sb + cur * (1 + KD) * elems;
+        const long long x0 = deposit_bits(blk >> a.log2chunks, a.outer_mask);
+        const long long col0 = (blk & cmask) << 5;
         for (int j = 0; j < m; ++j) {
             const int la = p.la[j], lb = p.lb[j];
             const int lo = la < lb ? la : lb, hi = la < lb ? lb : la;
@@ -953,21 +972,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_fwd_fused_df(const FwdFusedArgs
                     }
                 }
             }
-            __syncthreads();
+            __syncthreads();  // the next gate (or the next block's copies) may overwrite S
+        }
+        if (a.nbuf == 2) {
+            cur ^= 1;
+        } else {
+            if (nxt < a.n_blocks) load(nxt, Sb);
+            cp_async_commit_df();
         }
     }
+    cp_async_wait_df<0>();
+}
+
+template <class K>
+cudaError_t launch_resident_df(K kernel, const FwdFusedArgs &a, int sms, size_t smem, cudaStream_t s) {
+    int per_sm = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    const long long grid = std::min<long long>(a.n_blocks, (long long)sms * std::max(per_sm, 1));
+    kernel<<<(unsigned)grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <int MODE>
-cudaError_t launch_fused_df_mode(const FwdFusedArgs &a, int grid, size_t smem, cudaStream_t s) {
+cudaError_t launch_fused_df_mode(const FwdFusedArgs &a, int sms, size_t smem, cudaStream_t s) {
     switch (a.kdirs) {
-        case 0: k_fwd_fused_df<MODE, 0><<<grid, kThreads, smem, s>>>(a); break;
-        case 1: k_fwd_fused_df<MODE, 1><<<grid, kThreads, smem, s>>>(a); break;
-        case 2: k_fwd_fused_df<MODE, 2><<<grid, kThreads, smem, s>>>(a); break;
-        case 3: k_fwd_fused_df<MODE, 3><<<grid, kThreads, smem, s>>>(a); break;
-        default: k_fwd_fused_df<MODE, 4><<<grid, kThreads, smem, s>>>(a); break;
+        case 0: return launch_resident_df(k_fwd_fused_df<MODE, 0>, a, sms, smem, s);
+        case 1: return launch_resident_df(k_fwd_fused_df<MODE, 1>, a, sms, smem, s);
+        case 2: return launch_resident_df(k_fwd_fused_df<MODE, 2>, a, sms, smem, s);
+        case 3: return launch_resident_df(k_fwd_fused_df<MODE, 3>, a, sms, smem, s);
+        default: return launch_resident_df(k_fwd_fused_df<MODE, 4>, a, sms, smem, s);
     }
-    return cudaGetLastError();
 }
 
 template <int MODE>
@@ -1064,16 +1099,16 @@ cudaError_t init_sweep_attributes_df64() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_bwd_dir_df2<kParity4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kDirDfSmem);
-    const int fmax = (int)fused_smem_bytes(kMaxWindow, kMaxDirs, kMaxPassGates, 1);
+    const int fmax = (int)kMaxFusedSmem;
     if (e == cudaSuccess) e = fused_df_attributes<kGeneral>(fmax);
     if (e == cudaSuccess) e = fused_df_attributes<kParity4>(fmax);
     return e;
 }
 
-cudaError_t launch_fwd_fused_df64(const FwdFusedArgs &a, int grid, cudaStream_t s) {
-    const size_t smem = fused_smem_bytes(a.pass.q, a.kdirs, a.pass.m, 1);
-    return a.mode == kGeneral ? launch_fused_df_mode<kGeneral>(a, grid, smem, s)
-                              : launch_fused_df_mode<kParity4>(a, grid, smem, s);
+cudaError_t launch_fwd_fused_df64(const FwdFusedArgs &a, int sms, cudaStream_t s) {
+    const size_t smem = fused_smem_bytes(a.pass.q, a.kdirs, a.pass.m, a.nbuf);
+    return a.mode == kGeneral ? launch_fused_df_mode<kGeneral>(a, sms, smem, s)
+                              : launch_fused_df_mode<kParity4>(a, sms, smem, s);
 }
 
 void launch_init_unit_df64(double2 *psi0, const int32_t *cols, int B, int log2B, long long n_store,
