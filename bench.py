@@ -354,7 +354,8 @@ def run_ours(args):
                 "repeats": args.repeats, "batched_s_all": tb, "plain_s_all": tp,
                 "timing": "median of the repeats, wall clock of the synchronous host call",
                 "bitwise_equal": bool(np.array_equal(fb, fp)), "columns_per_tile": info["columns_per_tile"],
-                "autotune_ms": info["tune_ms"], "setup_s": setup_s, "first_call_s": first_s,
+                "autotune_ms": info["tune_ms"], "fusion_window": info["fusion_window"],
+                "fusion_autotune_ms": info["fusion_tune_ms"], "setup_s": setup_s, "first_call_s": first_s,
                 "fp64_tflops_batched": flops / batched_s / 1e12,
                 "workload": "256 problems: n in {8,10,12}, depth in {3,5,7,9}, t~U[0.1,1], U~U[2,8], "
                             "general gates, f + grad + 1 HVP each, full basis sums (seed 301)"}
@@ -616,12 +617,50 @@ def run_ours(args):
                       "5 launches after a warm-up; 2 flops per FMA")
         return out
 
+    if args.convergence:
+        # The paper's convergence setting (Sec. "Comparison with the MPO
+        # method"): spinful chain of 8 sites, periodic, 4th-order Trotter
+        # initialisation (21 layers), one gate per layer (translation
+        # invariant), parity gates; t = 1 (the paper does not give t), no
+        # noise.  A bounded number of trust-region steps (HVP-tCG, FP64 or
+        # double-float) over translation-representative basis sums.
+        prob = w.make_problem(8, 21, 1.0, sigma=0.0, order=4, periodic=True, tied=True, structure=1)
+        ctx = rq.Context(local).setup_problem(prob)
+        ctx.set_translation(2)
+        ctx.set_arithmetic(1 if args.df64_only else 0)
+        n = prob.n
+        st = rq.tr_state(radius=0.01, max_radius=0.1)
+        G = prob.gates.copy()
+        t0 = time.perf_counter()
+        f0 = ctx.cost(G)
+        recs = [{"step": 0, "f": f0, "fro2": 2 * 2 ** n + 2 * f0,
+                 "rel_err": (max(2 * 2 ** n + 2 * f0, 0.0) / 2 ** n) ** 0.5, "s": time.perf_counter() - t0}]
+        for it in range(args.convergence):
+            t0 = time.perf_counter()
+            G = ctx.tr_step(G, st)
+            f = st.f_new if st.accepted else st.f
+            recs.append({"step": it + 1, "f": f, "fro2": 2 * 2 ** n + 2 * f,
+                         "rel_err": (max(2 * 2 ** n + 2 * f, 0.0) / 2 ** n) ** 0.5, "rho": st.rho,
+                         "accepted": bool(st.accepted), "n_inner": st.n_inner, "tcg_exit": st.tcg_exit,
+                         "radius": st.radius, "grad_norm": st.grad_norm, "s": time.perf_counter() - t0})
+            print(json.dumps(recs[-1]), file=sys.stderr, flush=True)
+        info = ctx.info()
+        unit_err = max(float(np.abs(G[p].conj().T @ G[p] - np.eye(4)).max()) for p in range(prob.n_params))
+        print(json.dumps({"mode": "convergence", "workload": "spinful chain, 8 sites (n = 16), periodic, J = 1, "
+                          "U = 4, t = 1; 21 layers (4th-order Trotter start), one parity gate per layer "
+                          f"({prob.n_gates} gates, {prob.n_params} parameters); translation-representative "
+                          "basis sums (shift 2 sites)", "arith": "df64" if args.df64_only else "fp64",
+                          "columns": info["columns"], "columns_per_tile": info["columns_per_tile"],
+                          "error_definition": "||C - U||_F^2 = 2 * 2^n + 2 f; rel_err = sqrt of that / 2^n",
+                          "max_unitarity_error": unit_err, "steps": recs}), flush=True)
+        ctx.close()
+        return
     if args.cost_only:     # profiling cases only: cost evaluations with or without fusion
         prob = make_workload(args, 0)
         ctx = rq.Context(local, stream=stream.cuda_stream).setup_problem(prob)
         ctx.set_arithmetic(1 if args.df64_only else 0)
         ctx.set_fusion(args.fusion)
-        B = min(512, 1 << prob.n)
+        B = args.tile or min(512, 1 << prob.n)
         ctx.set_tile(B, 1)
         g_d = torch.from_numpy(prob.gates.copy()).to(dev)
         f_d = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -816,6 +855,8 @@ def main():
     ap.add_argument("--no-fusion", action="store_true", help="skip the fused-vs-unfused forward measurement")
     ap.add_argument("--no-full", action="store_true", help="skip the whole 65536-column evaluation")
     ap.add_argument("--repeats", type=int, default=5, help="repeats of the batched-vs-plain comparison (median)")
+    ap.add_argument("--convergence", type=int, default=0,
+                    help="run that many trust-region steps of the 8-site 21-layer convergence workload and exit")
     ap.add_argument("--cost-only", action="store_true", help="run cost evaluations only (profiling cases only)")
     ap.add_argument("--df64-only", action="store_true", help="with --cost-only: double-float arithmetic")
     ap.add_argument("--fusion", type=int, default=0, help="with --cost-only: fusion window (0 = off)")
