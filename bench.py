@@ -605,16 +605,18 @@ def run_ours(args):
         import ctypes
         lib = ctypes.CDLL(_build.PEAK_LIB)
         out = {}
-        for name in ("fp64", "fp32"):
-            fn = getattr(lib, f"pp_{name}_fma_rate")
+        for name, sym in (("fp64", "pp_fp64_fma_rate"), ("fp32", "pp_fp32_fma_rate"),
+                          ("fp64_mma", "pp_fp64_mma_rate")):
+            fn = getattr(lib, sym)
             fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
             tf, ms = ctypes.c_double(), ctypes.c_double()
             with ClockSampler(local) as clk:
                 rc = fn(local, 5, ctypes.byref(tf), ctypes.byref(ms))
             out[name] = {"tflops": tf.value if rc == 0 else None, "ms_per_launch": ms.value, "rc": rc,
                          "clocks": clk.summary()}
-        out["how"] = ("8 independent FMA chains per thread, 2 CTAs of 256 threads per SM, CUDA events over "
-                      "5 launches after a warm-up; 2 flops per FMA")
+        out["how"] = ("8 independent FMA chains per thread (fp64_mma: 8 chains of mma.sync m8n8k4 f64 per "
+                      "warp, 512 flops each), 2 CTAs of 256 threads per SM, CUDA events over 5 launches after "
+                      "a warm-up; 2 flops per FMA")
         return out
 
     if args.convergence:
