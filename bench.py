@@ -675,7 +675,7 @@ def run_ours(args):
                           "plan": ctx.fusion_info(), "columns_per_tile": B, "f_last_tile": float(f_d.item())}))
         return
     if args.parity_only:   # profiling cases only: the parity-gate sweep alone
-        par = measure(1, args.steps, args.warmup, args.tile)
+        par = measure(1, args.steps, args.warmup, args.tile, arith=1 if args.df64_only else 0)
         if rank == 0:
             print(json.dumps({"mode": "parity only (profiling)", "value": par["value"], "unit": UNIT,
                               "ms_per_step": par["ms_per_step"], "gpu_launches": par["launches"]}))
@@ -860,7 +860,8 @@ def main():
     ap.add_argument("--convergence", type=int, default=0,
                     help="run that many trust-region steps of the 8-site 21-layer convergence workload and exit")
     ap.add_argument("--cost-only", action="store_true", help="run cost evaluations only (profiling cases only)")
-    ap.add_argument("--df64-only", action="store_true", help="with --cost-only: double-float arithmetic")
+    ap.add_argument("--df64-only", action="store_true",
+                    help="with --cost-only or --parity-only: double-float arithmetic")
     ap.add_argument("--fusion", type=int, default=0, help="with --cost-only: fusion window (0 = off)")
     ap.add_argument("--sites", type=int, default=8, help="chain sites (n = 2 * sites); profiling cases only")
     ap.add_argument("--depth", type=int, default=11, help="brickwall layers; profiling cases only")

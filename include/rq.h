@@ -257,9 +257,10 @@ rq_status rq_set_checkpointing(rq_ctx *ctx, int interval);
 /* Window fusion of the forward pass (Sec. "Brick wall circuit layout": the
  * gates of a layer act on disjoint qubits and commute).  max_window_qubits 0
  * (default): every gate is one pass over the tile, in circuit order.  3..6:
- * after the leading run of disjoint gates, consecutive gates -- reordered
- * only past gates on disjoint qubits, with which they commute -- whose
- * qubits fit in a window of that many stored qubits form one pass: a CTA
+ * after the leading run of disjoint gates, each pass starts at the next gate
+ * and takes, one at a time, the later gate that fits in a window of that many
+ * stored qubits, moves only past gates on disjoint qubits (with which it
+ * commutes) and adds the fewest new qubits to the window: a CTA
  * holds [2^q amplitudes x 32 columns] of the state (and of each tangent) in
  * shared memory, applies the pass's gates (at most 16) there, and writes to
  * HBM only the checkpoints the backward pass needs (every state of a

@@ -103,6 +103,29 @@ def test_sixteen_qubits_sampled(rq, structure):
     assert_close(hv2, hv, prob.n, what="hvp")
 
 
+@pytest.mark.parametrize("structure", [0, 1])
+def test_eighteen_qubits_largest_target_that_fits(rq, structure):
+    """n = 18 (9 sites): the largest chain whose target store fits one GPU
+    (C(18, 9)^2 complex128 entries = 37.8 GB of sector blocks; n = 20 is
+    refused in test_size_limits).  Columns from small particle-number
+    sectors keep the oracle's per-sector eigendecompositions cheap; the
+    sweeps cost the same for every column."""
+    prob = w.make_problem(9, 5, 0.5, seed=1801, structure=structure)
+    X = w.random_directions(prob.n_params, 1, 1802)
+    cols = [0, (1 << 17) | 1, (1 << 9) | (1 << 3), (0b111111111 << 9) | 0b111111110]
+    f, g, hv, _ = oracle_eval(prob, cols, X, chunk=4)
+    ctx = _ctx(rq, prob)
+    assert ctx.info()["target_entries"] == 48620 ** 2
+    fs, gs, hs = 0.0, np.zeros_like(g), np.zeros_like(hv)
+    for j in cols:
+        ctx.set_columns(j, j + 1)
+        a = ctx.hvp(prob.gates, X)
+        fs, gs, hs = fs + a[0], gs + a[1], hs + a[2]
+    assert abs(fs - f) <= 1e-12 * max(abs(f), 1e-6 * 2 ** 18)
+    assert_close(gs, g, prob.n, what="rgrad")
+    assert_close(hs, hv, prob.n, what="hvp")
+
+
 # ------------------------------------------------------------ edge cases ----
 
 def test_empty_range_and_additivity_and_determinism(rq):
