@@ -38,20 +38,23 @@
 // CTA; a later kernel sums the partials in CTA order (deterministic).
 //
 // General gates use three real multiply-adds per complex product instead of
-// four (Gauss's three-multiplication form): for m = a + ib and x = u + iv,
-//   m x = (k - b (u + v)) + i (k + a (v - u)),  k = u (a + b),
-// with a + b tabulated once per gate (in shared memory) and u + v, v - u
-// formed once per amplitude and reused by every output and environment entry
-// that amplitude meets.  The environment entry conj(l) x, l = p + iq, is kept
-// as three sums, K1 = sum u (p - q), K2 = sum p (v - u), K3 = sum q (u + v),
-// with Re = K1 + K3 and Im = K1 + K2 formed once per thread before the block
-// reduction.  GB300's FP64 pipe is the bound of these kernels, and this cuts
-// the FP64 instructions of a general-gate item by 12.5-17 %.  Parity gates
-// touch two entries per row, where the per-amplitude sums cost as much as
-// they save, so their backward steps keep the four-product form; their
-// forward step with tangents uses three products, the state's sums serving
-// both its own rows and the tangents' (88 instead of 96 per item and
-// direction).
+// four (Gauss's three-multiplication form), in the variant that needs one sum
+// per amplitude: for m = a + ib and x = u + iv,
+//   m x = (k - (a + b) v) + i (k + (b - a) u),  k = a (u + v),
+// with a, -(a + b) and b - a tabulated once per gate (in shared memory) and
+// S = u + v formed once per amplitude and reused by every output and
+// environment entry that amplitude meets.  The environment entry conj(l) x,
+// l = p + iq, is the same form with m = conj(l): three sums
+// A1 = sum p S_x, A2 = sum (p - q) v, A3 = sum (p + q) u, with Re = A1 - A2
+// and Im = A1 - A3 formed once per thread before the block reduction (the
+// sums p - q, p + q of an adjoint amplitude serve its four entries).
+// GB300's FP64 pipe is the bound of these kernels; against four products per
+// complex product this cuts the FP64 instructions of a general-gate item by
+// 16-19 %.  Parity gates touch two entries per row: their gate applications
+// (forward steps, adjoint updates) use the same form, where the one sum per
+// amplitude costs less than the product it saves, and their environment
+// entries keep four products (two sums per adjoint amplitude would cost as
+// much as they save).
 #include "rq_items.cuh"
 
 #include <algorithm>
@@ -78,11 +81,11 @@ __device__ __forceinline__ void cmacc(double2 &acc, const double2 a, const doubl
 
 __device__ __forceinline__ double2 zero2() { return make_double2(0.0, 0.0); }
 
-// A general 4x4 complex matrix tabulated for the three-product form:
-// s = a + b, a, nb = -b of each entry m = a + ib, row-major (16-byte aligned,
-// so two neighbouring entries of a row load as one 128-bit shared load).
+// A 4x4 complex matrix tabulated for the three-product form: a, ns = -(a + b)
+// and d = b - a of each entry m = a + ib, row-major (16-byte aligned, so two
+// neighbouring entries of a row load as one 128-bit shared load).
 struct __align__(16) Mat3 {
-    double s[16], a[16], nb[16];
+    double a[16], ns[16], d[16];
 };
 
 // Tabulate G (adjoint = 0) or G^dagger (adjoint = 1) from 16 complex entries;
@@ -97,12 +100,14 @@ __device__ __forceinline__ void tabulate3(Mat3 &m, const double2 *g, int e, int 
         re = g[e].x;
         im = g[e].y;
     }
-    m.s[e] = re + im;
     m.a[e] = re;
-    m.nb[e] = -im;
+    m.ns[e] = -(re + im);
+    m.d[e] = im - re;
 }
 
-// An amplitude x = u + iv with its sums: u, S = u + v, D = v - u (and v).
+// An amplitude x = u + iv with its sums S = u + v and D = v - u (D only where
+// the amplitude is the conjugated factor of an environment entry; unused
+// sums are dropped by the compiler).
 struct Amp3 {
     double u, v, S, D;
 };
@@ -120,14 +125,14 @@ __device__ __forceinline__ Amp3 amp3(const double2 x) {
 __device__ __forceinline__ void matvec3(const Mat3 &m, const Amp3 (&x)[4], double2 (&y)[4]) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        double k = x[0].u * m.s[i * 4];
+        double k = m.a[i * 4] * x[0].S;
 #pragma unroll
-        for (int c = 1; c < 4; ++c) k = fma(x[c].u, m.s[i * 4 + c], k);
+        for (int c = 1; c < 4; ++c) k = fma(m.a[i * 4 + c], x[c].S, k);
         double re = k, im = k;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            re = fma(m.nb[i * 4 + c], x[c].S, re);
-            im = fma(m.a[i * 4 + c], x[c].D, im);
+            re = fma(m.ns[i * 4 + c], x[c].v, re);
+            im = fma(m.d[i * 4 + c], x[c].u, im);
         }
         y[i] = make_double2(re, im);
     }
@@ -138,21 +143,21 @@ __device__ __forceinline__ void matvec3_pair(const Mat3 &m, const Amp3 (&x)[4], 
                                              const Amp3 (&w)[4], double2 (&y)[4]) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        double k = x[0].u * m.s[i * 4];
+        double k = m.a[i * 4] * x[0].S;
 #pragma unroll
-        for (int c = 1; c < 4; ++c) k = fma(x[c].u, m.s[i * 4 + c], k);
+        for (int c = 1; c < 4; ++c) k = fma(m.a[i * 4 + c], x[c].S, k);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) k = fma(w[c].u, n.s[i * 4 + c], k);
+        for (int c = 0; c < 4; ++c) k = fma(n.a[i * 4 + c], w[c].S, k);
         double re = k, im = k;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            re = fma(m.nb[i * 4 + c], x[c].S, re);
-            im = fma(m.a[i * 4 + c], x[c].D, im);
+            re = fma(m.ns[i * 4 + c], x[c].v, re);
+            im = fma(m.d[i * 4 + c], x[c].u, im);
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            re = fma(n.nb[i * 4 + c], w[c].S, re);
-            im = fma(n.a[i * 4 + c], w[c].D, im);
+            re = fma(n.ns[i * 4 + c], w[c].v, re);
+            im = fma(n.d[i * 4 + c], w[c].u, im);
         }
         y[i] = make_double2(re, im);
     }
@@ -169,9 +174,9 @@ __device__ __forceinline__ void matvec3_blocks(const Mat3 &m, const Amp3 (&x)[4]
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int c0 = pcol(i, 0), c1 = pcol(i, 1);
-        const double k = fma(x[c1].u, m.s[i * 4 + c1], x[c0].u * m.s[i * 4 + c0]);
-        const double re = fma(m.nb[i * 4 + c1], x[c1].S, fma(m.nb[i * 4 + c0], x[c0].S, k));
-        const double im = fma(m.a[i * 4 + c1], x[c1].D, fma(m.a[i * 4 + c0], x[c0].D, k));
+        const double k = fma(m.a[i * 4 + c1], x[c1].S, m.a[i * 4 + c0] * x[c0].S);
+        const double re = fma(m.ns[i * 4 + c1], x[c1].v, fma(m.ns[i * 4 + c0], x[c0].v, k));
+        const double im = fma(m.d[i * 4 + c1], x[c1].u, fma(m.d[i * 4 + c0], x[c0].u, k));
         y[i] = make_double2(re, im);
     }
 }
@@ -182,41 +187,41 @@ __device__ __forceinline__ void matvec3_pair_blocks(const Mat3 &m, const Amp3 (&
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int c0 = pcol(i, 0), c1 = pcol(i, 1);
-        double k = x[c0].u * m.s[i * 4 + c0];
-        k = fma(x[c1].u, m.s[i * 4 + c1], k);
-        k = fma(w[c0].u, n.s[i * 4 + c0], k);
-        k = fma(w[c1].u, n.s[i * 4 + c1], k);
-        double re = fma(m.nb[i * 4 + c0], x[c0].S, k);
-        re = fma(m.nb[i * 4 + c1], x[c1].S, re);
-        re = fma(n.nb[i * 4 + c0], w[c0].S, re);
-        re = fma(n.nb[i * 4 + c1], w[c1].S, re);
-        double im = fma(m.a[i * 4 + c0], x[c0].D, k);
-        im = fma(m.a[i * 4 + c1], x[c1].D, im);
-        im = fma(n.a[i * 4 + c0], w[c0].D, im);
-        im = fma(n.a[i * 4 + c1], w[c1].D, im);
+        double k = m.a[i * 4 + c0] * x[c0].S;
+        k = fma(m.a[i * 4 + c1], x[c1].S, k);
+        k = fma(n.a[i * 4 + c0], w[c0].S, k);
+        k = fma(n.a[i * 4 + c1], w[c1].S, k);
+        double re = fma(m.ns[i * 4 + c0], x[c0].v, k);
+        re = fma(m.ns[i * 4 + c1], x[c1].v, re);
+        re = fma(n.ns[i * 4 + c0], w[c0].v, re);
+        re = fma(n.ns[i * 4 + c1], w[c1].v, re);
+        double im = fma(m.d[i * 4 + c0], x[c0].u, k);
+        im = fma(m.d[i * 4 + c1], x[c1].u, im);
+        im = fma(n.d[i * 4 + c0], w[c0].u, im);
+        im = fma(n.d[i * 4 + c1], w[c1].u, im);
         y[i] = make_double2(re, im);
     }
 }
 
-// Environment sums of conj(l_i) x_c over all 16 (i, c): K1 += u_c (p_i - q_i)
-// (p - q = -D of l), K2 += p_i D_c, K3 += q_i S_c.
-__device__ __forceinline__ void env3(double (&K1)[16], double (&K2)[16], double (&K3)[16], const Amp3 (&l)[4],
+// Environment sums of conj(l_i) x_c over all 16 (i, c): A1 += p_i S_c,
+// A2 += (p_i - q_i) v_c (p - q = -D of l), A3 += (p_i + q_i) u_c (p + q = S of l).
+__device__ __forceinline__ void env3(double (&A1)[16], double (&A2)[16], double (&A3)[16], const Amp3 (&l)[4],
                                      const Amp3 (&x)[4]) {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            K1[i * 4 + c] = fma(-l[i].D, x[c].u, K1[i * 4 + c]);
-            K2[i * 4 + c] = fma(l[i].u, x[c].D, K2[i * 4 + c]);
-            K3[i * 4 + c] = fma(l[i].v, x[c].S, K3[i * 4 + c]);
+            A1[i * 4 + c] = fma(l[i].u, x[c].S, A1[i * 4 + c]);
+            A2[i * 4 + c] = fma(-l[i].D, x[c].v, A2[i * 4 + c]);
+            A3[i * 4 + c] = fma(l[i].S, x[c].u, A3[i * 4 + c]);
         }
 }
 
-// E[i] = (K1 + K3, K1 + K2)
-__device__ __forceinline__ void env3_finish(const double (&K1)[16], const double (&K2)[16], const double (&K3)[16],
+// E[i] = (A1 - A2, A1 - A3)
+__device__ __forceinline__ void env3_finish(const double (&A1)[16], const double (&A2)[16], const double (&A3)[16],
                                             double2 (&E)[16]) {
 #pragma unroll
-    for (int i = 0; i < 16; ++i) E[i] = make_double2(K1[i] + K3[i], K1[i] + K2[i]);
+    for (int i = 0; i < 16; ++i) E[i] = make_double2(A1[i] - A2[i], A1[i] - A3[i]);
 }
 
 // ------------------------------------------------ pipelined item loads --
@@ -425,18 +430,18 @@ template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1) k_bwd_base(const BwdArgs a) {
     const int accumulate = a.accumulate;
     __shared__ double2 sg[16];
-    __shared__ Mat3 sgT3;  // G^dagger, general gates
+    __shared__ Mat3 sgT3;  // G^dagger, gates on two stored qubits
     if (threadIdx.x < 16) {
-        if (MODE == kGeneral) tabulate3(sgT3, a.gate, threadIdx.x, 1);
+        if (MODE != kParity2) tabulate3(sgT3, a.gate, threadIdx.x, 1);
         else sg[threadIdx.x] = a.gate[threadIdx.x];
     }
     __syncthreads();
     double2 E[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) E[i] = zero2();
-    double K1[16], K2[16], K3[16];
+    double A1[16], A2[16], A3[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) K1[i] = K2[i] = K3[i] = 0.0;
+    for (int i = 0; i < 16; ++i) A1[i] = A2[i] = A3[i] = 0.0;
     const long long Bm = (1LL << a.log2B) - 1;
     if constexpr (MODE == kGeneral || MODE == kParity4) {
         // gates on two stored qubits: pipelined item loads
@@ -464,7 +469,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_base(const BwdArgs a) {
                         Amp3 p[4];
 #pragma unroll
                         for (int c = 0; c < 4; ++c) p[c] = amp3(*slot(st, 4 + c));
-                        env3(K1, K2, K3, l, p);
+                        env3(A1, A2, A3, l, p);
                     }
                     if (a.update) {
                         double2 q[4];
@@ -486,11 +491,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_base(const BwdArgs a) {
                         cmacc(E[9], l[2], p[1]); cmacc(E[10], l[2], p[2]);
                     }
                     if (a.update) {
+                        Amp3 lx[4];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) lx[c] = amp3(l[c]);
                         double2 q[4];
-                        q[0] = zero2(); cmacc(q[0], sg[0], l[0]); cmacc(q[0], sg[12], l[3]);
-                        q[3] = zero2(); cmacc(q[3], sg[3], l[0]); cmacc(q[3], sg[15], l[3]);
-                        q[1] = zero2(); cmacc(q[1], sg[5], l[1]); cmacc(q[1], sg[9], l[2]);
-                        q[2] = zero2(); cmacc(q[2], sg[6], l[1]); cmacc(q[2], sg[10], l[2]);
+                        matvec3_blocks(sgT3, lx, q);
 #pragma unroll
                         for (int c = 0; c < 4; ++c) a.lam[off[c]] = q[c];
                     }
@@ -530,7 +535,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_base(const BwdArgs a) {
             }
         }
     }
-    if constexpr (MODE == kGeneral) env3_finish(K1, K2, K3, E);
+    if constexpr (MODE == kGeneral) env3_finish(A1, A2, A3, E);
     if (accumulate) block_reduce_store(E, a.part + (long long)blockIdx.x * kEnvDoubles);
 }
 
@@ -546,9 +551,9 @@ template <int MODE>
 __global__ void __launch_bounds__(kThreads, MODE == kGeneral ? 1 : 2) k_bwd_dir(const BwdArgs a) {
     __shared__ double2 sg[16];
     __shared__ double2 sx[16];
-    __shared__ Mat3 sgT3, sxT3;  // G^dagger, X^dagger, general gates
+    __shared__ Mat3 sgT3, sxT3;  // G^dagger, X^dagger, gates on two stored qubits
     if (threadIdx.x < 16) {
-        if (MODE == kGeneral) {
+        if (MODE != kParity2) {
             tabulate3(sgT3, a.gate, threadIdx.x, 1);
             tabulate3(sxT3, a.dir, threadIdx.x, 1);
         } else {
@@ -560,9 +565,9 @@ __global__ void __launch_bounds__(kThreads, MODE == kGeneral ? 1 : 2) k_bwd_dir(
     double2 E[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) E[i] = zero2();
-    double K1[16], K2[16], K3[16];
+    double A1[16], A2[16], A3[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) K1[i] = K2[i] = K3[i] = 0.0;
+    for (int i = 0; i < 16; ++i) A1[i] = A2[i] = A3[i] = 0.0;
     const long long Bm = (1LL << a.log2B) - 1;
     if constexpr (MODE == kGeneral) {
         extern __shared__ double2 pf[];
@@ -591,8 +596,8 @@ __global__ void __launch_bounds__(kThreads, MODE == kGeneral ? 1 : 2) k_bwd_dir(
                     p[c] = amp3(*slot(st, 8 + c));
                     dp[c] = amp3(*slot(st, 12 + c));
                 }
-                env3(K1, K2, K3, dl, p);
-                env3(K1, K2, K3, l, dp);
+                env3(A1, A2, A3, dl, p);
+                env3(A1, A2, A3, l, dp);
                 if (a.update) {
                     double2 q[4];
                     matvec3_pair(sgT3, dl, sxT3, l, q);  // G^dagger lambda' + X^dagger lambda
@@ -622,15 +627,14 @@ __global__ void __launch_bounds__(kThreads, MODE == kGeneral ? 1 : 2) k_bwd_dir(
                     cmacc(E[idx[u][0] * 4 + idx[u][1]], l[idx[u][0]], dp[idx[u][1]]);
                 }
                 if (a.update) {
+                    Amp3 dlx[4], lx[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        dlx[c] = amp3(dl[c]);
+                        lx[c] = amp3(l[c]);
+                    }
                     double2 q[4];
-                    q[0] = zero2(); cmacc(q[0], sg[0], dl[0]); cmacc(q[0], sg[12], dl[3]);
-                    cmacc(q[0], sx[0], l[0]); cmacc(q[0], sx[12], l[3]);
-                    q[3] = zero2(); cmacc(q[3], sg[3], dl[0]); cmacc(q[3], sg[15], dl[3]);
-                    cmacc(q[3], sx[3], l[0]); cmacc(q[3], sx[15], l[3]);
-                    q[1] = zero2(); cmacc(q[1], sg[5], dl[1]); cmacc(q[1], sg[9], dl[2]);
-                    cmacc(q[1], sx[5], l[1]); cmacc(q[1], sx[9], l[2]);
-                    q[2] = zero2(); cmacc(q[2], sg[6], dl[1]); cmacc(q[2], sg[10], dl[2]);
-                    cmacc(q[2], sx[6], l[1]); cmacc(q[2], sx[10], l[2]);
+                    matvec3_pair_blocks(sgT3, dlx, sxT3, lx, q);  // G^dagger lambda' + X^dagger lambda
 #pragma unroll
                     for (int c = 0; c < 4; ++c) a.dlam[off[c]] = q[c];
                 }
@@ -669,7 +673,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kGeneral ? 1 : 2) k_bwd_dir(
             }
         }
     }
-    if constexpr (MODE == kGeneral) env3_finish(K1, K2, K3, E);
+    if constexpr (MODE == kGeneral) env3_finish(A1, A2, A3, E);
     block_reduce_store(E, a.part + (long long)blockIdx.x * kEnvDoubles);
 }
 

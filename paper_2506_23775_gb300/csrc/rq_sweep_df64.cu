@@ -121,33 +121,36 @@ __device__ __forceinline__ float2 df_add(float ah, float al, float bh, float bl)
 }
 
 // General gates in the forward sweep use the three-product form (as the FP64
-// kernels do): for m = a + ib and x = u + iv, m x = (k - b (u + v)) +
-// i (k + a (v - u)) with k = u (a + b).  In df64 a product term costs as much
-// as before but the sums u + v, v - u are formed once per amplitude and serve
-// all four rows, and a + b once per gate entry.
+// kernels do), in its one-sum variant: for m = a + ib and x = u + iv,
+// m x = (k - (a + b) v) + i (k + (b - a) u) with k = a (u + v).  In df64 a
+// product term costs as much as before but the sum u + v is formed once per
+// amplitude and serves all four rows, and a, -(a + b), b - a once per gate
+// entry.
 struct MatDf3 {
-    float2 s[16], a[16], nb[16];  // a + b, a, -b
+    float2 a[16], ns[16], d[16];  // a, -(a + b), b - a
 };
 
 __device__ __forceinline__ void tabulate_df3(MatDf3 &m, const float4 *g, int e) {
     const float4 x = g[e];
-    m.s[e] = df_add(x.x, x.y, x.z, x.w);
+    const float2 s = df_add(x.x, x.y, x.z, x.w);
     m.a[e] = make_float2(x.x, x.y);
-    m.nb[e] = make_float2(-x.z, -x.w);
+    m.ns[e] = make_float2(-s.x, -s.y);
+    m.d[e] = df_add(x.z, x.w, -x.x, -x.y);
 }
 
-// x = u + iv with S = u + v, D = v - u
+// x = u + iv with S = u + v
 struct AmpDf3 {
-    float uh, ul;
-    float2 S, D;
+    float uh, ul, vh, vl;
+    float2 S;
 };
 
 __device__ __forceinline__ AmpDf3 amp_df3(const float4 x) {
     AmpDf3 r;
     r.uh = x.x;
     r.ul = x.y;
+    r.vh = x.z;
+    r.vl = x.w;
     r.S = df_add(x.x, x.y, x.z, x.w);
-    r.D = df_add(x.z, x.w, -x.x, -x.y);
     return r;
 }
 
@@ -163,14 +166,14 @@ __device__ __forceinline__ void df_matvec3(const MatDf3 &m, const AmpDf3 (&x)[4]
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         Acc k;
-        acc_set(k, x[0].uh, x[0].ul, m.s[i * 4].x, m.s[i * 4].y);
+        acc_set(k, m.a[i * 4].x, m.a[i * 4].y, x[0].S.x, x[0].S.y);
 #pragma unroll
-        for (int c = 1; c < 4; ++c) acc_mac(k, x[c].uh, x[c].ul, m.s[i * 4 + c].x, m.s[i * 4 + c].y);
+        for (int c = 1; c < 4; ++c) acc_mac(k, m.a[i * 4 + c].x, m.a[i * 4 + c].y, x[c].S.x, x[c].S.y);
         CAcc q{k, k};
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            acc_mac(q.re, m.nb[i * 4 + c].x, m.nb[i * 4 + c].y, x[c].S.x, x[c].S.y);
-            acc_mac(q.im, m.a[i * 4 + c].x, m.a[i * 4 + c].y, x[c].D.x, x[c].D.y);
+            acc_mac(q.re, m.ns[i * 4 + c].x, m.ns[i * 4 + c].y, x[c].vh, x[c].vl);
+            acc_mac(q.im, m.d[i * 4 + c].x, m.d[i * 4 + c].y, x[c].uh, x[c].ul);
         }
         y[i] = fin(q);
     }
@@ -182,18 +185,18 @@ __device__ __forceinline__ void df_matvec3_pair(const MatDf3 &m, const AmpDf3 (&
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         Acc k;
-        acc_set(k, t[0].uh, t[0].ul, m.s[i * 4].x, m.s[i * 4].y);
+        acc_set(k, m.a[i * 4].x, m.a[i * 4].y, t[0].S.x, t[0].S.y);
 #pragma unroll
-        for (int c = 1; c < 4; ++c) acc_mac(k, t[c].uh, t[c].ul, m.s[i * 4 + c].x, m.s[i * 4 + c].y);
+        for (int c = 1; c < 4; ++c) acc_mac(k, m.a[i * 4 + c].x, m.a[i * 4 + c].y, t[c].S.x, t[c].S.y);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc_mac(k, x[c].uh, x[c].ul, n.s[i * 4 + c].x, n.s[i * 4 + c].y);
+        for (int c = 0; c < 4; ++c) acc_mac(k, n.a[i * 4 + c].x, n.a[i * 4 + c].y, x[c].S.x, x[c].S.y);
         CAcc q{k, k};
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            acc_mac(q.re, m.nb[i * 4 + c].x, m.nb[i * 4 + c].y, t[c].S.x, t[c].S.y);
-            acc_mac(q.re, n.nb[i * 4 + c].x, n.nb[i * 4 + c].y, x[c].S.x, x[c].S.y);
-            acc_mac(q.im, m.a[i * 4 + c].x, m.a[i * 4 + c].y, t[c].D.x, t[c].D.y);
-            acc_mac(q.im, n.a[i * 4 + c].x, n.a[i * 4 + c].y, x[c].D.x, x[c].D.y);
+            acc_mac(q.re, m.ns[i * 4 + c].x, m.ns[i * 4 + c].y, t[c].vh, t[c].vl);
+            acc_mac(q.re, n.ns[i * 4 + c].x, n.ns[i * 4 + c].y, x[c].vh, x[c].vl);
+            acc_mac(q.im, m.d[i * 4 + c].x, m.d[i * 4 + c].y, t[c].uh, t[c].ul);
+            acc_mac(q.im, n.d[i * 4 + c].x, n.d[i * 4 + c].y, x[c].uh, x[c].ul);
         }
         y[i] = fin(q);
     }
