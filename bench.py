@@ -40,14 +40,14 @@ HBM_FALLBACK_GBS = 6800.0
 # DRAM traffic of one full (not first-layer) FP64 bwd_gate_dir launch of this
 # workload (2^14 x 512 items: n = 16, general gates, 512-column tile):
 # dram__bytes_read.sum + dram__bytes_write.sum of the same kernel captured at
-# n = 14 (2^12 x 512 items: 536.93 + 111.32 MB) scaled by the items, 4x (the
+# n = 14 (2^12 x 512 items: 536.98 + 111.07 MB) scaled by the items, 4x (the
 # DRAM-traffic ncu summary under profiles/).  Algorithmic bytes of that
 # launch: 2^14 * 512 * 5 * 4 * 16 = 2.684e9.  The figure holds only for the
 # kernel source it was taken on, so the sources are hashed and compared at
 # run time.
-TRAFFIC = {"kernel": "bwd_gate_dir", "bytes_per_launch": 2593003520,
+TRAFFIC = {"kernel": "bwd_gate_dir", "bytes_per_launch": 2592171008,
            "algorithmic_bytes_per_launch": 2684354560,
-           "sha256": "f9f212151ddf82286e32a689fd02cd9a0b982f62270beb90f4c672271cf57307",
+           "sha256": "9b3c9d6b7a9a9a3fe8ba5ba2ee50299b06310570bdb40d4f25df349a97be16a6",
            "sources": ("paper_2506_23775_gb300/csrc/rq_sweep.cu", "paper_2506_23775_gb300/csrc/rq_items.cuh",
                        "paper_2506_23775_gb300/csrc/rq_internal.h")}
 
