@@ -330,7 +330,8 @@ def run_ours(args):
     def measure_batched():
         """256 independent problems (n in {8,10,12}, depth in {3,5,7,9}, t ~ U[0.1,1],
         U ~ U[2,8], seed 301): f + grad + 1 HVP of every problem, as one CUDA-graph
-        launch (batched) and one problem after another (plain)."""
+        launch (batched, tile, sweep grid and fusion window autotuned) and one
+        problem after another (plain, every sweep filling the GPU as if alone)."""
         probs = w.batch_problems(256, seed=301)
         b = rq.Batch(local)
         t0 = time.perf_counter()
@@ -342,25 +343,51 @@ def run_ours(args):
         t0 = time.perf_counter()
         b.hvp(gates, dirs)                      # autotune + capture + first replay
         first_s = time.perf_counter() - t0
-        tb, tp = [], []
-        for _ in range(args.repeats):          # alternating, so drifts hit both alike
-            t0 = time.perf_counter()
-            fb, _, _ = b.hvp(gates, dirs)
-            tb.append(time.perf_counter() - t0)
-            t0 = time.perf_counter()
-            fp, _, _ = b.hvp(gates, dirs, plain=True)
-            tp.append(time.perf_counter() - t0)
-        batched_s, plain_s = statistics.median(tb), statistics.median(tp)
         info = b.info()
+
+        def timed(plain, reps):
+            ts, res = [], None
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                res = b.hvp(gates, dirs, plain=plain)
+                ts.append(time.perf_counter() - t0)
+            return ts, res
+
+        tb, (fb, gb, hb) = timed(False, args.repeats)
+        b.set_grid(0)                           # plain: each problem's sweeps fill the GPU
+        tp, (fp, gp, hp) = timed(True, args.repeats)
+        tb0, (fb0, _, _) = timed(False, 2)     # the batched graph at that grid, for reference
+        batched_s, plain_s = statistics.median(tb), statistics.median(tp)
         b.close()
+        # plain at each problem's own configuration: one context per problem
+        # with the automatic tile (as large as memory allows for one problem),
+        # timed after a warm-up call (set-up excluded)
+        alone_s = 0.0
+        for p, g, d in zip(probs, gates, dirs):
+            with rq.Context(local) as ctx:
+                ctx.setup_problem(p)
+                ctx.hvp(g, d)
+                t0 = time.perf_counter()
+                ctx.hvp(g, d)
+                alone_s += time.perf_counter() - t0
+        dev = max(max(abs(x - y) / abs(y) for x, y in zip(fb, fp)),
+                  max(float(np.abs(x - y).max() / np.abs(y).max()) for x, y in zip(hb, hp)))
         flops = sum(9 * p.n_gates * 32.0 * 4 ** p.n for p in probs)
         return {"problems": len(probs), "unit": "problem evals/s",
                 "batched": len(probs) / batched_s, "plain": len(probs) / plain_s,
                 "speedup": plain_s / batched_s, "batched_s": batched_s, "plain_s": plain_s,
                 "repeats": args.repeats, "batched_s_all": tb, "plain_s_all": tp,
-                "timing": "median of the repeats, wall clock of the synchronous host call",
-                "bitwise_equal": bool(np.array_equal(fb, fp)), "columns_per_tile": info["columns_per_tile"],
-                "autotune_ms": info["tune_ms"], "fusion_window": info["fusion_window"],
+                "batched_grid0_s": statistics.median(tb0),
+                "plain_alone": len(probs) / alone_s, "plain_alone_s": alone_s,
+                "speedup_vs_alone": alone_s / batched_s,
+                "timing": "median of the repeats, wall clock of the synchronous host call; batched repeats "
+                          "first, then plain (the batch's contexts and tile, grid 0); plain_alone: the sum of "
+                          "one warm call per problem, each on its own context at the automatic tile",
+                "max_rel_dev_batched_vs_plain": dev,
+                "bitwise_equal_at_same_grid": bool(np.array_equal(fb0, fp)),
+                "columns_per_tile": info["columns_per_tile"], "autotune_ms": info["tune_ms"],
+                "grid_items_per_thread": info["grid_items"], "grid_autotune_ms": info["grid_tune_ms"],
+                "fusion_window": info["fusion_window"],
                 "fusion_autotune_ms": info["fusion_tune_ms"], "setup_s": setup_s, "first_call_s": first_s,
                 "fp64_tflops_batched": flops / batched_s / 1e12,
                 "workload": "256 problems: n in {8,10,12}, depth in {3,5,7,9}, t~U[0.1,1], U~U[2,8], "

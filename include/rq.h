@@ -136,6 +136,7 @@ typedef struct {
     int64_t workspace_bytes;        /* device memory held by the context */
     int64_t target_entries;         /* complex entries of the stored U blocks */
     int64_t kernel_launches;        /* kernels launched since rq_create */
+    int ctas_per_sweep;             /* grid of the sweep kernels (rq_set_grid) */
 } rq_info_t;
 
 /* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to
@@ -241,6 +242,21 @@ rq_status rq_set_checks(rq_ctx *ctx, int enable);
  * cannot be captured (the legacy default stream) falls back to direct
  * launches. */
 rq_status rq_set_graphs(rq_ctx *ctx, int enable);
+
+/* Grid of the sweep kernels (throughput vs latency).  0 (default): every
+ * sweep launches enough CTAs to fill the GPU (two per SM when the tile has a
+ * full block of items for each, otherwise at most one per SM and one
+ * warp-sized chunk of items per CTA), the fastest schedule for a context that
+ * has the GPU to itself.  m > 0: at most as many CTAs as give every thread m
+ * items of a full sweep, so that each CTA's fixed costs (gate tables, the
+ * environment reduction, the pipeline's first load) are paid over more items;
+ * meant for contexts whose sweeps run concurrently with other contexts'
+ * (rq_batch, a server), which fill the rest of the GPU.  The results change
+ * only in the rounding of the environment sums (a different reduction tree),
+ * and stay reproducible for a given m.  Reallocates the partial-sum buffers;
+ * RQ_EINVAL unless 0 <= m <= 2^20.  rq_get_info reports the grid
+ * (ctas_per_sweep). */
+rq_status rq_set_grid(rq_ctx *ctx, int min_items_per_thread);
 
 /* Checkpointing of the forward pass (memory vs recomputation).  interval 1
  * (default): every intermediate state of a tile is kept (the paper's
@@ -377,7 +393,7 @@ rq_status rq_cost_static(rq_ctx *ctx, const double *gates, double *f);
  * Every problem has its own context (target blocks, workspace, stream).  One
  * evaluation of the whole batch is one CUDA-graph launch whose branches run
  * the problems concurrently; results are bitwise those of each problem
- * evaluated alone.  The columns-per-tile of the batch is autotuned at the
+ * evaluated alone with the same sweep grid (rq_batch_set_grid).  The columns-per-tile of the batch is autotuned at the
  * first evaluation (rq_batch_set_tile(b, 0)) or fixed (power of two).
  *
  * rq_batch_hvp: host arrays.  gates: every problem's [n_params][4][4]
@@ -405,6 +421,18 @@ rq_status rq_batch_info(const rq_batch *b, int *n_problems, int *columns_per_til
  * window in use and the autotuner's timings (ms for windows 0, 4, 5, 6; -1
  * where not timed). */
 rq_status rq_batch_set_fusion(rq_batch *b, int max_window_qubits);
+/* Sweep grid of every problem of the batch (rq_set_grid).  min_items_per_thread
+ * -1 (default): autotuned at the first evaluation after the tile size, by
+ * timing the captured gradient evaluation of the batch with 0, 8, 16, 32 and
+ * 64 items per thread and keeping the fastest (the problems' concurrent
+ * sweeps share the GPU, so each needs fewer CTAs than alone); 0: every
+ * problem's sweeps fill the GPU as if alone; m > 0: that grid for every
+ * problem.  The grid applies to the graph and to plain = 1 alike (batched and
+ * plain results stay bitwise equal); a one-at-a-time comparison at its own
+ * best grid sets 0 first.  rq_batch_grid_info: the grid in use and the
+ * autotuner's timings (ms for 0, 8, 16, 32, 64; -1 where not timed). */
+rq_status rq_batch_set_grid(rq_batch *b, int min_items_per_thread);
+rq_status rq_batch_grid_info(const rq_batch *b, int *min_items_per_thread, double *tune_ms);
 rq_status rq_batch_fusion_info(const rq_batch *b, int *window, double *tune_ms);
 const char *rq_batch_last_error(const rq_batch *b);
 

@@ -15,6 +15,11 @@
 // the whole batch and the fastest is kept.  Then the fusion window of the
 // forward passes (gates per pass, rq_set_fusion: off, 4, 5 or 6 stored
 // qubits) is tuned the same way at that tile, unless the caller fixed it.
+// Before that, the sweep grid of the problems (rq_set_grid: 0, 8, 16, 32 or
+// 64 items per thread) is tuned on a captured gradient evaluation of the
+// batch: the problems' sweeps share the GPU, so each needs fewer CTAs than
+// it would alone, and fewer CTAs pay the per-CTA set-up and environment
+// reduction fewer times.
 #include "rq_internal.h"
 
 #include <algorithm>
@@ -45,6 +50,9 @@ struct rq_batch {
     int fuse_req = -1;             // fusion window for every problem; -1: autotune
     int fuse_q = 0;                // the window in use
     std::vector<double> fuse_ms;   // per candidate window 0, 4, 5, 6 (-1: not timed)
+    int grid_req = -1;             // sweep grid (rq_set_grid) of every problem; -1: autotune
+    int grid_items = 0;            // the grid in use
+    std::vector<double> grid_ms;   // per candidate 0, 8, 16, 32, 64 items per thread (-1: not timed)
 };
 
 namespace {
@@ -178,6 +186,33 @@ rq_status apply_cap(rq_batch *b, int cap) {
     return RQ_OK;
 }
 
+rq_status apply_grid(rq_batch *b, int m) {
+    for (rq_ctx *c : b->ctxs) {
+        const rq_status st = rq_set_grid(c, m);
+        if (st != RQ_OK) return ctx_fail(b, c, st);
+    }
+    b->grid_items = m;
+    drop_graph(b);
+    return RQ_OK;
+}
+
+// Capture the evaluation of the given kind and time one replay after a
+// warm-up replay.
+rq_status time_graph(rq_batch *b, int env_mode, cudaEvent_t e0, cudaEvent_t e1, double &ms_out) {
+    rq_status st = capture(b, 0, env_mode);
+    if (st != RQ_OK) return st;
+    cudaGraphLaunch(b->exec, b->main);  // warm-up
+    cudaEventRecord(e0, b->main);
+    cudaGraphLaunch(b->exec, b->main);
+    cudaEventRecord(e1, b->main);
+    if (cudaEventSynchronize(e1) != cudaSuccess)
+        return bfail(b, RQ_ECUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms_out = ms;
+    return RQ_OK;
+}
+
 rq_status apply_fusion(rq_batch *b, int q) {
     for (rq_ctx *c : b->ctxs) {
         const rq_status st = rq_set_fusion(c, q);
@@ -241,26 +276,39 @@ rq_status autotune(rq_batch *b) {
     }
     b->tile_cap = best;
     rq_status st = apply_cap(b, best);
-    // gates per pass: the fusion window, timed on the same cost-only proxy
+    // sweep grid: timed on a gradient evaluation (the backward kernels carry
+    // the per-CTA environment reductions that fewer CTAs save)
+    const int grids[5] = {0, 8, 16, 32, 64};
+    b->grid_ms.assign(5, -1.0);
+    if (st == RQ_OK && b->grid_req < 0) {
+        int best_m = 0;
+        double best_m_ms = 1e300;
+        for (int i = 0; i < 5 && st == RQ_OK; ++i) {
+            double ms = 0;
+            st = apply_grid(b, grids[i]);
+            if (st == RQ_OK) st = time_graph(b, 1, e0, e1, ms);
+            if (st != RQ_OK) break;
+            b->grid_ms[i] = ms;
+            if (ms < best_m_ms) {
+                best_m_ms = ms;
+                best_m = grids[i];
+            }
+        }
+        if (st == RQ_OK) st = apply_grid(b, best_m);
+    } else if (st == RQ_OK) {
+        st = apply_grid(b, b->grid_req);
+    }
+    // gates per pass: the fusion window, timed on the cost-only proxy
     const int wins[4] = {0, 4, 5, 6};
     b->fuse_ms.assign(4, -1.0);
     if (st == RQ_OK && b->fuse_req < 0) {
         int best_q = 0;
         double best_q_ms = 1e300;
         for (int i = 0; i < 4 && st == RQ_OK; ++i) {
+            double ms = 0;
             st = apply_fusion(b, wins[i]);
-            if (st == RQ_OK) st = capture(b, 0, 0);
+            if (st == RQ_OK) st = time_graph(b, 0, e0, e1, ms);
             if (st != RQ_OK) break;
-            cudaGraphLaunch(b->exec, b->main);  // warm-up
-            cudaEventRecord(e0, b->main);
-            cudaGraphLaunch(b->exec, b->main);
-            cudaEventRecord(e1, b->main);
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-                st = bfail(b, RQ_ECUDA, "fusion autotune: %s", cudaGetErrorString(cudaGetLastError()));
-                break;
-            }
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
             b->fuse_ms[i] = ms;
             if (ms < best_q_ms) {
                 best_q_ms = ms;
@@ -338,6 +386,7 @@ rq_status rq_batch_add(rq_batch *b, const rq_target *t, const rq_circuit *c, int
         return st;
     }
     st = rq_set_fusion(ctx, b->fuse_q);  // the batch's current window
+    if (st == RQ_OK) st = rq_set_grid(ctx, b->grid_items);
     if (st != RQ_OK) {
         bfail(b, st, "problem %zu: %s", b->ctxs.size(), rq_last_error(ctx));
         rq_destroy(ctx);
@@ -363,7 +412,8 @@ rq_status rq_batch_set_tile(rq_batch *b, int columns_per_tile) {
         return bfail(b, RQ_EINVAL, "columns_per_tile %d is not 0 or a power of two", columns_per_tile);
     b->tile_cap = columns_per_tile;
     b->tile_fixed = columns_per_tile > 0;
-    b->tuned = columns_per_tile > 0 && b->fuse_req >= 0;  // else the fusion window is tuned at the next evaluation
+    // else the grid or the fusion window is tuned at the next evaluation
+    b->tuned = columns_per_tile > 0 && b->fuse_req >= 0 && b->grid_req >= 0;
     if (columns_per_tile > 0) return apply_cap(b, columns_per_tile);
     return RQ_OK;
 }
@@ -374,16 +424,15 @@ rq_status rq_batch_hvp(rq_batch *b, const double *gates, const double *dirs, int
     if (b->ctxs.empty()) return bfail(b, RQ_ESTATE, "empty batch");
     if (!gates || !f || k < 0 || (k > 0 && !dirs)) return bfail(b, RQ_EINVAL, "invalid arguments");
     RB_CUDA(cudaSetDevice(b->device));
-    if (!b->tuned) {
-        rq_status st = ensure_buffers(b, k);
-        if (st == RQ_OK) st = autotune(b);
-        if (st != RQ_OK) return st;
-    }
     rq_status st = ensure_buffers(b, k);
     if (st != RQ_OK) return st;
     const size_t g = sizeof(double2) * (size_t)b->gtotal;
     RB_CUDA(cudaMemcpyAsync(b->d_gates, gates, g, cudaMemcpyHostToDevice, b->main));
     if (k > 0) RB_CUDA(cudaMemcpyAsync(b->d_dirs, dirs, g * k, cudaMemcpyHostToDevice, b->main));
+    if (!b->tuned) {  // the autotuner's evaluations see these gates
+        st = autotune(b);
+        if (st != RQ_OK) return st;
+    }
     if (plain) {
         for (rq_ctx *c : b->ctxs) {
             st = rq::prepare_capacity(c, std::max(k, 1));
@@ -412,6 +461,30 @@ rq_status rq_batch_info(const rq_batch *b, int *n_problems, int *columns_per_til
     if (columns_per_tile) *columns_per_tile = b->tile_cap;
     if (tune_ms)
         for (int i = 0; i < 4; ++i) tune_ms[i] = i < (int)b->tune_ms.size() ? b->tune_ms[i] : -1.0;
+    return RQ_OK;
+}
+
+rq_status rq_batch_set_grid(rq_batch *b, int min_items_per_thread) {
+    if (!b) return RQ_EINVAL;
+    if (min_items_per_thread < -1 || min_items_per_thread > (1 << 20))
+        return bfail(b, RQ_EINVAL, "min_items_per_thread %d is neither -1 (autotune) nor in [0, 2^20]",
+                     min_items_per_thread);
+    RB_CUDA(cudaSetDevice(b->device));
+    RB_CUDA(cudaStreamSynchronize(b->main));
+    b->grid_req = min_items_per_thread;
+    if (min_items_per_thread >= 0) {
+        b->grid_ms.assign(5, -1.0);
+        return apply_grid(b, min_items_per_thread);
+    }
+    b->tuned = false;  // tune again at the next evaluation
+    return RQ_OK;
+}
+
+rq_status rq_batch_grid_info(const rq_batch *b, int *min_items_per_thread, double *tune_ms) {
+    if (!b) return RQ_EINVAL;
+    if (min_items_per_thread) *min_items_per_thread = b->grid_items;
+    if (tune_ms)
+        for (int i = 0; i < 5; ++i) tune_ms[i] = i < (int)b->grid_ms.size() ? b->grid_ms[i] : -1.0;
     return RQ_OK;
 }
 

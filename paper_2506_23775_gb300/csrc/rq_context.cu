@@ -299,9 +299,16 @@ rq_status rebuild_tiles_impl(rq_ctx *ctx) {
     // one CTA per SM, so more would run in two waves), and at least one
     // warp-sized chunk of items per CTA (the kernels hand chunks to CTAs round
     // robin, so a small sweep still reaches every SM).
+    // With rq_set_grid(m), at most the CTAs that give every thread m items: a
+    // sweep that shares the GPU with other problems' sweeps (a batch, a
+    // server) pays its per-CTA set-up and environment reduction fewer times.
     const long long full = (long long)ctx->sms * rq::kCtasPerSm * rq::kThreads;
-    const int ncta = (int)(items >= full ? (long long)ctx->sms * rq::kCtasPerSm
-                                         : std::min<long long>(ctx->sms, (items + 31) / 32));
+    int ncta = (int)(items >= full ? (long long)ctx->sms * rq::kCtasPerSm
+                                   : std::min<long long>(ctx->sms, (items + 31) / 32));
+    if (ctx->grid_items > 0) {
+        const long long per_cta = (long long)rq::kThreads * ctx->grid_items;
+        ncta = (int)std::max<long long>(1, std::min<long long>(ncta, (items + per_cta - 1) / per_cta));
+    }
     std::vector<int32_t> cols;
     std::vector<double> wts;
     std::vector<int> tpar;
@@ -486,6 +493,14 @@ rq_status rq_set_tile(rq_ctx *ctx, int columns_per_tile, int max_dirs) {
     return rebuild_tiles(ctx);
 }
 
+rq_status rq_set_grid(rq_ctx *ctx, int min_items_per_thread) {
+    if (!ctx) return RQ_EINVAL;
+    if (min_items_per_thread < 0 || min_items_per_thread > (1 << 20))
+        return fail(ctx, RQ_EINVAL, "min_items_per_thread %d outside [0, 2^20]", min_items_per_thread);
+    ctx->grid_items = min_items_per_thread;
+    return ctx->ready ? rebuild_tiles(ctx) : RQ_OK;
+}
+
 rq_status rq_set_checkpointing(rq_ctx *ctx, int interval) {
     if (!ctx) return RQ_EINVAL;
     if (!ctx->ready) return fail(ctx, RQ_ESTATE, "no target set up");
@@ -575,6 +590,7 @@ rq_status rq_get_info(const rq_ctx *ctx, rq_info_t *info) {
     info->max_dirs = ctx->kc;
     info->workspace_bytes = ctx->problem_bytes + ctx->work_bytes + ctx->small_bytes;
     info->target_entries = ctx->u_entries;
+    info->ctas_per_sweep = ctx->ncta;
     return RQ_OK;
 }
 

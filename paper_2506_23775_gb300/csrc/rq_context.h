@@ -48,6 +48,7 @@ struct rq_ctx {
     double2 *d_psi = nullptr, *d_dpsi = nullptr, *d_lam = nullptr, *d_dlam = nullptr;
     double *d_part = nullptr, *d_partd = nullptr;
     int ncta = 0;
+    int grid_items = 0;  // rq_set_grid: minimum items per thread of a full sweep (0: fill the GPU)
     double *d_env = nullptr, *d_envd = nullptr;
     int envd_cap = 0;
     double *d_fpart = nullptr, *d_facc = nullptr;

@@ -19,11 +19,11 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "lib
 RQ_OK, RQ_EINVAL, RQ_ENOMEM, RQ_ECUDA, RQ_ETIMEOUT, RQ_ESTATE = 0, -1, -2, -3, -4, -5
 
 # Every symbol declared in include/rq.h.
-EXPORTS = ("rq_create", "rq_destroy", "rq_setup_target", "rq_set_columns", "rq_set_tile",
+EXPORTS = ("rq_create", "rq_destroy", "rq_setup_target", "rq_set_columns", "rq_set_tile", "rq_set_grid",
            "rq_cost", "rq_grad", "rq_hvp", "rq_cost_dev", "rq_grad_dev", "rq_hvp_dev",
            "rq_tr_step", "rq_target_column", "rq_get_info", "rq_profile_start", "rq_profile_stop",
            "rq_cost_static", "rq_set_gradient_space", "rq_batch_create", "rq_batch_destroy",
-           "rq_batch_add", "rq_batch_set_tile", "rq_batch_hvp", "rq_batch_info", "rq_batch_last_error",
+           "rq_batch_add", "rq_batch_set_tile", "rq_batch_set_grid", "rq_batch_grid_info", "rq_batch_hvp", "rq_batch_info", "rq_batch_last_error",
            "rq_batch_set_fusion", "rq_batch_fusion_info",
            "rq_set_arithmetic", "rq_set_translation", "rq_hessian", "rq_set_checkpointing",
            "rq_set_graphs", "rq_set_checks", "rq_set_first_layer", "rq_set_fusion", "rq_fusion_info",
@@ -55,7 +55,8 @@ class RQInfo(C.Structure):
                 ("structure", C.c_int), ("amplitudes_per_column", C.c_int64),
                 ("columns", C.c_int64), ("columns_per_tile", C.c_int), ("n_tiles", C.c_int),
                 ("max_dirs", C.c_int), ("workspace_bytes", C.c_int64),
-                ("target_entries", C.c_int64), ("kernel_launches", C.c_int64)]
+                ("target_entries", C.c_int64), ("kernel_launches", C.c_int64),
+                ("ctas_per_sweep", C.c_int)]
 
 
 class RQKernelStat(C.Structure):
@@ -85,6 +86,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "rq_setup_target": ([vp, C.POINTER(RQTarget), C.POINTER(RQCircuit)], C.c_int),
         "rq_set_columns": ([vp, i64, i64], C.c_int),
         "rq_set_tile": ([vp, C.c_int, C.c_int], C.c_int),
+        "rq_set_grid": ([vp, C.c_int], C.c_int),
         "rq_cost": ([vp, dp, dp], C.c_int),
         "rq_grad": ([vp, dp, dp, dp], C.c_int),
         "rq_hvp": ([vp, dp, dp, C.c_int, dp, dp, dp], C.c_int),
@@ -110,6 +112,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "rq_batch_destroy": ([vp], C.c_int),
         "rq_batch_add": ([vp, C.POINTER(RQTarget), C.POINTER(RQCircuit), C.POINTER(C.c_int)], C.c_int),
         "rq_batch_set_tile": ([vp, C.c_int], C.c_int),
+        "rq_batch_set_grid": ([vp, C.c_int], C.c_int),
+        "rq_batch_grid_info": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_double)], C.c_int),
         "rq_batch_hvp": ([vp, dp, dp, C.c_int, C.c_int, dp, dp, dp], C.c_int),
         "rq_batch_info": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int), dp], C.c_int),
         "rq_batch_last_error": ([vp], C.c_char_p),
@@ -258,6 +262,10 @@ class Context:
 
     def set_tile(self, columns_per_tile: int = 0, max_dirs: int = 0):
         self._check(self._lib.rq_set_tile(self._h, int(columns_per_tile), int(max_dirs)))
+
+    def set_grid(self, min_items_per_thread: int):
+        """0: sweeps fill the GPU; m > 0: at most the CTAs that give each thread m items."""
+        self._check(self._lib.rq_set_grid(self._h, int(min_items_per_thread)))
 
     def info(self) -> dict:
         i = RQInfo()
@@ -413,9 +421,18 @@ class Batch:
         q = C.c_int()
         fms = (C.c_double * 4)()
         self._check(self._lib.rq_batch_fusion_info(self._h, C.byref(q), fms))
+        m = C.c_int()
+        gms = (C.c_double * 5)()
+        self._check(self._lib.rq_batch_grid_info(self._h, C.byref(m), gms))
         return {"n_problems": n.value, "columns_per_tile": t.value,
                 "tune_ms": dict(zip((64, 128, 256, 512), list(ms))),
-                "fusion_window": q.value, "fusion_tune_ms": dict(zip((0, 4, 5, 6), list(fms)))}
+                "fusion_window": q.value, "fusion_tune_ms": dict(zip((0, 4, 5, 6), list(fms))),
+                "grid_items": m.value, "grid_tune_ms": dict(zip((0, 8, 16, 32, 64), list(gms)))}
+
+    def set_grid(self, min_items_per_thread: int):
+        """Sweep grid of every problem (rq_set_grid): -1 autotune at the next
+        evaluation, 0 each problem fills the GPU as if alone, m > 0 fixed."""
+        self._check(self._lib.rq_batch_set_grid(self._h, int(min_items_per_thread)))
 
     def set_fusion(self, max_window_qubits: int):
         """-1: autotune the fusion window at the next evaluation; 0: off; 3..6."""

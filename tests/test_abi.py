@@ -76,4 +76,4 @@ def test_struct_layouts_match_header(tmp_path):
     # rq_tr_state: 5 doubles, int, 5 doubles, 3 ints (padded)
     assert ctypes.sizeof(rq.RQTarget) == 4 * 3 + 4 + 8 * 3 + 8
     assert ctypes.sizeof(rq.RQCircuit) == 16 + 16
-    assert ctypes.sizeof(rq.RQInfo) == 4 * 4 + 8 * 2 + 4 * 3 + 4 + 8 * 3
+    assert ctypes.sizeof(rq.RQInfo) == 4 * 4 + 8 * 2 + 4 * 3 + 4 + 8 * 3 + 4 + 4  # ctas_per_sweep, padding
