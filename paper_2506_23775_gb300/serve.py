@@ -11,8 +11,11 @@ so repeated requests skip the set-up; new contexts are built by host worker
 threads while the loop keeps admitting and collecting work.
 
 Every evaluation runs the library's kernels in the same order as the same
-request evaluated alone on a context with the same tile size, so a result in
-the mix equals the result alone bit for bit.
+request evaluated alone on a context with the same tile size and sweep grid,
+so a result in the mix equals the result alone bit for bit.  With a sweep
+grid of m items per thread (rq_set_grid) each request's sweeps take fewer
+CTAs, so more requests share the GPU at once and each pays its per-CTA
+costs fewer times.
 """
 from __future__ import annotations
 
@@ -64,11 +67,15 @@ def admission_key(req: "Request", now: float, aging: float, fp64_flops_per_s: fl
     return work_flops(req) / fp64_flops_per_s - aging * (now - req.arrival)
 
 
-def gpu_width(p, tile: int, sms: int = 152) -> float:
+def gpu_width(p, tile: int, sms: int = 152, grid: int = 0) -> float:
     """Fraction of the GPU one sweep kernel of this problem fills (its items
-    over two 256-thread CTAs per SM)."""
+    over two 256-thread CTAs per SM; with a sweep grid of ``grid`` items per
+    thread, the threads of its CTAs)."""
     n_store = (1 << (p.n - 1)) if p.structure == 1 else (1 << p.n)
-    return min(1.0, n_store / 4 * tile / (sms * 2 * 256))
+    items = n_store / 4 * tile
+    if grid > 0:
+        items = min(items, -(-items // (256 * grid)) * 256)
+    return min(1.0, items / (sms * 2 * 256))
 
 
 def footprint_bytes(p, tile: int, k: int = 1) -> int:
@@ -99,12 +106,15 @@ class Server:
     "sjf" (shortest estimated work first); ``aging``: with "sjf", seconds of
     estimated work forgiven per second a request has waited, so a large
     request cannot wait forever behind a stream of small ones (0: pure
-    shortest-first).
+    shortest-first).  ``grid``: sweep grid of every context (rq_set_grid:
+    0 fills the GPU per sweep; m > 0 at most the CTAs that give each thread m
+    items, so that concurrent requests share the GPU).
     """
 
     def __init__(self, device: int = 0, memory_budget: Optional[int] = None, max_inflight: int = 8,
                  tile: int = 128, contexts_per_problem: int = 2, setup_workers: int = 2,
-                 policy: str = "sjf", aging: float = 0.0, fp64_flops_per_s: float = 1.2e12):
+                 policy: str = "sjf", aging: float = 0.0, fp64_flops_per_s: float = 1.2e12,
+                 grid: int = 0):
         import concurrent.futures as cf
 
         import torch
@@ -118,6 +128,7 @@ class Server:
         self.budget = memory_budget
         self.max_inflight = max_inflight
         self.tile = tile
+        self.grid = grid
         self.per_problem = contexts_per_problem
         self.slots: Dict[tuple, List[_Slot]] = collections.defaultdict(list)
         self.building: Dict[tuple, list] = collections.defaultdict(list)   # futures of contexts being set up
@@ -146,6 +157,8 @@ class Server:
         stream = self.torch.cuda.Stream(device=self.dev)
         ctx = self.rq.Context(self.device, stream=stream.cuda_stream).setup_problem(p)
         ctx.set_tile(tile, 1)
+        if self.grid:
+            ctx.set_grid(self.grid)
         return _Slot(ctx, stream, key, tile, need)
 
     def _harvest_builds(self):
@@ -224,7 +237,7 @@ class Server:
             # A request whose problem has no free context does not block others.
             if self.policy == "sjf":
                 waiting.sort(key=lambda r: admission_key(r, t, self.aging, self.rate))
-            width = sum(gpu_width(r.problem, s.tile, self.sms) for r, s, _, _ in inflight)
+            width = sum(gpu_width(r.problem, s.tile, self.sms, self.grid) for r, s, _, _ in inflight)
             still = []
             for req in waiting:
                 if len(inflight) >= self.max_inflight or (self.policy == "sjf" and inflight and width >= 1.0):
@@ -238,7 +251,7 @@ class Server:
                 req.admitted = now()
                 ev, out = self._launch(req, s)
                 inflight.append((req, s, ev, out))
-                width += gpu_width(req.problem, s.tile, self.sms)
+                width += gpu_width(req.problem, s.tile, self.sms, self.grid)
             waiting = still
             # collect finished work
             rest = []

@@ -30,10 +30,11 @@ def _stream(serve):
     return serve.poisson_stream(probs, kinds, rate_hz=400.0, seed=502, k=2)
 
 
-def test_results_in_the_mix_equal_results_alone(mods):
+@pytest.mark.parametrize("grid", [0, 8])
+def test_results_in_the_mix_equal_results_alone(mods, grid):
     rq, serve = mods
     reqs = _stream(serve)
-    srv = serve.Server(0, memory_budget=8 << 30, max_inflight=4, tile=64, contexts_per_problem=2)
+    srv = serve.Server(0, memory_budget=8 << 30, max_inflight=4, tile=64, contexts_per_problem=2, grid=grid)
     stats = srv.run(reqs)
     srv.close()
     assert stats["requests"] == len(reqs) and stats["reused"] > 0
@@ -45,6 +46,7 @@ def test_results_in_the_mix_equal_results_alone(mods):
         with rq.Context(0) as ctx:
             ctx.setup_problem(p)
             ctx.set_tile(min(64, 1 << p.n), 1)
+            ctx.set_grid(grid)
             if r.kind == "cost":
                 assert ctx.cost(p.gates) == r.f
             elif r.kind == "grad":
