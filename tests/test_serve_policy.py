@@ -34,3 +34,16 @@ def test_aging_lets_a_long_waiting_large_request_through():
     assert serve.admission_key(big, t, 1.0, 1.2e12) < serve.admission_key(small_new, t, 1.0, 1.2e12)
     # without aging it never does
     assert serve.admission_key(big, t, 0.0, 1.2e12) > serve.admission_key(small_new, t, 0.0, 1.2e12)
+
+
+def test_gpu_width_with_a_sweep_grid():
+    """Width = threads of the sweep's CTAs over two 256-thread CTAs per SM;
+    a grid of m items per thread cuts the CTAs of a large sweep, not of a
+    sweep that already has fewer items than threads."""
+    p = w.make_problem(6, 3, 0.5, seed=1)      # n = 12: 1024 items per column
+    full = serve.gpu_width(p, 128, sms=152)    # 131072 items: 1.68 GPUs of threads
+    assert full == 1.0
+    narrow = serve.gpu_width(p, 128, sms=152, grid=32)
+    assert narrow == 16 * 256 / (152 * 2 * 256)  # ceil(131072 / (256 * 32)) = 16 CTAs
+    small = w.make_problem(3, 3, 0.5, seed=2)  # n = 6: 16 items per column
+    assert serve.gpu_width(small, 4, sms=152, grid=8) == serve.gpu_width(small, 4, sms=152) == 64 / (152 * 512)
