@@ -370,8 +370,8 @@ def run_ours(args):
                 t0 = time.perf_counter()
                 ctx.hvp(g, d)
                 alone_s += time.perf_counter() - t0
-        dev = max(max(abs(x - y) / abs(y) for x, y in zip(fb, fp)),
-                  max(float(np.abs(x - y).max() / np.abs(y).max()) for x, y in zip(hb, hp)))
+        dev = max(max(abs(x - y) / max(abs(y), 1e-300) for x, y in zip(fb, fp)),
+                  max(float(np.abs(x - y).max() / max(np.abs(y).max(), 1e-300)) for x, y in zip(hb, hp)))
         flops = sum(9 * p.n_gates * 32.0 * 4 ** p.n for p in probs)
         return {"problems": len(probs), "unit": "problem evals/s",
                 "batched": len(probs) / batched_s, "plain": len(probs) / plain_s,
