@@ -219,6 +219,21 @@ rq_status rq_set_translation(rq_ctx *ctx, int shift_sites);
  * its items.  enable = 0 sweeps every item. */
 rq_status rq_set_first_layer(rq_ctx *ctx, int enable);
 
+/* Last-layer support, on by default.  The backward sweep of column j starts
+ * from U|j> (paper Eq. f_target_sum_unit_vec), which lies in j's particle-
+ * number sector (the chain Hamiltonians conserve the up and down counts, or
+ * the one count of the spinless chain), and the gates of the trailing run of
+ * pairwise disjoint gates (the last brickwall layer) change it only on their
+ * own qubits.  So at gate l of the run an item (the four amplitudes the gate
+ * mixes) can be nonzero only if the bits outside the qubits of gates l..g of
+ * the run can be completed to a state of j's sector; the backward kernels
+ * (FP64 and double-float) skip the other items, whose adjoint amplitudes and
+ * environment terms are zero (a warp skips when all its 32 columns do).
+ * General gates with a chain target only (parity tiles and dense targets
+ * sweep every item).  The results equal the full sweeps up to the order of
+ * the sums.  enable = 0 sweeps every item. */
+rq_status rq_set_last_layer(rq_ctx *ctx, int enable);
+
 /* Gate validation, off by default.  With enable = 1 every rq_cost, rq_grad,
  * rq_hvp, rq_tr_step (each evaluation inside it) and rq_hessian call, and
  * the _dev variants (which then copy the gates to the host and synchronise

@@ -176,6 +176,53 @@ void plan_passes(rq_ctx *ctx) {
         }
         rest.swap(left);
     }
+    mark_tail(ctx);
+}
+
+bool fused_schedule(const rq_ctx *ctx) {
+    return ctx->fuse_q > 2 && ctx->ckpt_r == 1 && ctx->B >= 32 && (int)ctx->plan.size() < ctx->g;
+}
+
+// Last-layer support: the trailing run of pairwise disjoint gates of the
+// order the backward pass walks (the plan's execution order under the fused
+// schedule, else the circuit order), which it visits first.  For the gate at
+// position pos of the run, the adjoint state it reads differs from U|j> only
+// on the qubits of the run's later gates, and U|j> lives in j's particle-
+// number sector (spinful chain: up and down counts; spinless chain: one
+// count; a dense target has no sectors).  General gates only: parity tiles
+// store 2^(n-1) amplitudes without the implied qubit's bit.  Called when the
+// plan or the tile configuration (and so the schedule) changes.
+void mark_tail(rq_ctx *ctx) {
+    for (GateGeom &gg : ctx->geo) {
+        gg.tail = 0;
+        gg.f_up = gg.f_dn = 0;
+        gg.up_out = gg.dn_out = gg.up_mask = gg.dn_mask = 0;
+    }
+    if (!ctx->last_layer || ctx->structure != 0 || ctx->tgt.model == 2 || (int)ctx->order.size() != ctx->g) return;
+    const int n = ctx->n;
+    long long upm, dnm;
+    if (ctx->tgt.model == 0) {  // qubit q = (site q, up) for q < L, (site q - L, down) after; stored bit n - 1 - q
+        upm = ((1LL << ctx->L) - 1) << (n - ctx->L);
+        dnm = (1LL << (n - ctx->L)) - 1;
+    } else {                    // spinless chain: one particle number over all qubits
+        upm = (1LL << n) - 1;
+        dnm = 0;
+    }
+    const bool fused = fused_schedule(ctx);
+    long long F = 0;
+    for (int pos = ctx->g - 1; pos >= 0; --pos) {
+        GateGeom &gg = ctx->geo[fused ? ctx->order[pos] : pos];
+        const long long b = gate_bits(gg);
+        if (F & b) break;
+        F |= b;
+        gg.tail = 1;
+        gg.up_mask = upm;
+        gg.dn_mask = dnm;
+        gg.up_out = upm & ~F;
+        gg.dn_out = dnm & ~F;
+        gg.f_up = __builtin_popcountll(F & upm);
+        gg.f_dn = __builtin_popcountll(F & dnm);
+    }
 }
 
 // Column lists of the current range: one list (general gates) or the even-
@@ -351,6 +398,8 @@ rq_status rebuild_tiles_impl(rq_ctx *ctx) {
     }
     ctx->tile_parity = tpar;
     ctx->n_tiles = (int)tpar.size();
+    ctx->cols_h = cols;
+    mark_tail(ctx);  // the schedule (fused or not) may have changed with the tile
     if (!cols.empty()) {
         RQ_CUDA(cudaMemcpyAsync(ctx->d_cols, cols.data(), cols.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                                 ctx->stream));
@@ -512,6 +561,14 @@ rq_status rq_set_checkpointing(rq_ctx *ctx, int interval) {
 rq_status rq_set_first_layer(rq_ctx *ctx, int enable) {
     if (!ctx) return RQ_EINVAL;
     ctx->first_layer = enable != 0;
+    if (ctx->ready) plan_passes(ctx);
+    ++ctx->version;
+    return RQ_OK;
+}
+
+rq_status rq_set_last_layer(rq_ctx *ctx, int enable) {
+    if (!ctx) return RQ_EINVAL;
+    ctx->last_layer = enable != 0;
     if (ctx->ready) plan_passes(ctx);
     ++ctx->version;
     return RQ_OK;

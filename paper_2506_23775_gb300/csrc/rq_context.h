@@ -44,6 +44,7 @@ struct rq_ctx {
     int user_B = 0, user_kc = 0;
     std::vector<int> tile_parity;
     int32_t *d_cols = nullptr;
+    std::vector<int32_t> cols_h;  // host copy of the column table (tiles x B; -1: padding)
     // workspace
     double2 *d_psi = nullptr, *d_dpsi = nullptr, *d_lam = nullptr, *d_dlam = nullptr;
     double *d_part = nullptr, *d_partd = nullptr;
@@ -93,6 +94,7 @@ struct rq_ctx {
     long long version = 0, graph_clock = 0;
     int checks = 0;  // validate the gates of every call (unitarity, parity pattern)
     bool first_layer = true;  // FP64 sweeps of the leading disjoint gates visit only nonzero items
+    bool last_layer = true;   // backward sweeps of the trailing disjoint gates skip items with zero adjoint
     // window fusion of the forward pass (rq_set_fusion): execution order of
     // the gates (a reordering of commuting disjoint gates) and its passes
     int fuse_q = 0;  // largest window in stored bits; 0: off (every gate its own pass, original order)
@@ -182,6 +184,12 @@ void drop_graphs(rq_ctx *ctx);
 void free_problem(rq_ctx *ctx);
 int ilog2(long long v);
 void plan_passes(rq_ctx *ctx);
+// Whether evaluations run the fused forward schedule (and walk the plan's
+// execution order backwards): a fusion window, every state kept, whole
+// 32-column chunks per tile, and a plan with at least one multi-gate pass.
+bool fused_schedule(const rq_ctx *ctx);
+// Last-layer marks of the gates for the backward order the evaluations use.
+void mark_tail(rq_ctx *ctx);
 long long state_slots(const rq_ctx *ctx);
 long long bytes_per_column(const rq_ctx *ctx, int kc);
 rq_status rebuild_tiles(rq_ctx *ctx);

@@ -34,6 +34,35 @@ using namespace rqc;
 
 namespace rqc {
 
+namespace {
+// Number of c-bit patterns of m bits with lo <= c <= hi.
+double count_window(int m, int lo, int hi) {
+    double s = 0.0, binom = 1.0;  // C(m, c), c ascending
+    for (int c = 0; c <= m; ++c) {
+        if (c >= lo && c <= hi) s += binom;
+        binom = binom * (m - c) / (c + 1);
+    }
+    return s;
+}
+}  // namespace
+
+// Items of a last-layer gate with work in tile ti (the profile's algorithmic
+// counts; the kernels visit every item and skip the others): per column j,
+// 2^(bits the run has touched, less the gate's own) times the patterns of
+// the untouched up and down bits that can be completed to j's sector.
+double tail_items(const rq_ctx *ctx, const GateGeom &geo, int ti) {
+    const int mu = __builtin_popcountll(geo.up_out), md = __builtin_popcountll(geo.dn_out);
+    const int other = ctx->n - 2 - mu - md;
+    double total = 0.0;
+    for (int b = 0; b < ctx->B; ++b) {
+        const long long j = ctx->cols_h[(size_t)ti * ctx->B + b];
+        if (j < 0) continue;
+        const int nu = __builtin_popcountll(j & geo.up_mask), nd = __builtin_popcountll(j & geo.dn_mask);
+        total += std::ldexp(count_window(mu, nu - geo.f_up, nu) * count_window(md, nd - geo.f_dn, nd), other);
+    }
+    return total;
+}
+
 // One evaluation over the column range; every pointer is device memory.
 // env_mode: 0 no gradient environments (cost, or HVPs whose Riemannian
 // correction is not needed), 1 accumulate them, 2 reuse the accumulators of the
@@ -102,7 +131,7 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
     const bool backward = want_env || k > 0;
     // fused forward passes: every checkpoint slot exists (interval 1) and a
     // tile has whole 32-column chunks
-    const bool fused = ctx->fuse_q > 2 && r == 1 && B >= 32 && (int)ctx->plan.size() < g;
+    const bool fused = fused_schedule(ctx);  // the order the last-layer marks were made for
     const int n_chunks = k == 0 ? 1 : (k + ctx->kc - 1) / ctx->kc;
     for (int ch = 0; ch < n_chunks; ++ch) {
         const int d0 = ch * ctx->kc;
@@ -281,6 +310,12 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                     a.cols = cols;
                     a.n_items = (long long)B << __builtin_popcountll(geo.free_bits);
                 }
+                // last-layer support: the kernels skip the items whose adjoint
+                // amplitudes are zero (they read the column table for j)
+                if (geo.tail) a.cols = cols;
+                // items with work, for the profile's algorithmic counts
+                const double live = ctx->prof_on && geo.tail && !(geo.restricted && first_layer)
+                                        ? tail_items(ctx, geo, ti) : (double)a.n_items;
                 for (int d = 0; d < kd; ++d) {
                     rq::BwdArgs b = a;
                     b.dlam = ctx->d_dlam + d * tile;
@@ -291,8 +326,8 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                     {
                         const double amps = geo.mode == rq::kParity2 ? 2.0 : 4.0;
                         const double cm = geo.mode == rq::kGeneral ? 16.0 : (geo.mode == rq::kParity4 ? 8.0 : 4.0);
-                        ProfScope ps(ctx, kFamBwdDir, (double)b.n_items * 8.0 * cm * (2 + 2 * b.update),
-                                     (double)b.n_items * amps * sizeof(double2) * (4 + b.update));
+                        ProfScope ps(ctx, kFamBwdDir, live * 8.0 * cm * (2 + 2 * b.update),
+                                     live * amps * sizeof(double2) * (4 + b.update));
                         if (df) rq::launch_bwd_dir_df64(b, ctx->ncta, s);
                         else rq::launch_bwd_dir(b, ctx->ncta, s);
                     }
@@ -307,8 +342,8 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                     {
                         const double amps = geo.mode == rq::kParity2 ? 2.0 : 4.0;
                         const double cm = geo.mode == rq::kGeneral ? 16.0 : (geo.mode == rq::kParity4 ? 8.0 : 4.0);
-                        ProfScope ps(ctx, kFamBwdBase, (double)a.n_items * 8.0 * cm * (a.accumulate + a.update),
-                                     (double)a.n_items * amps * sizeof(double2) * (1 + a.accumulate + a.update));
+                        ProfScope ps(ctx, kFamBwdBase, live * 8.0 * cm * (a.accumulate + a.update),
+                                     live * amps * sizeof(double2) * (1 + a.accumulate + a.update));
                         if (df) rq::launch_bwd_base_df64(a, ctx->ncta, s);
                         else rq::launch_bwd_base(a, ctx->ncta, s);
                     }

@@ -37,6 +37,20 @@ struct GateGeom {
     // value.  restricted = 0: every item.
     int restricted = 0;
     long long free_bits = 0, fixed_bits = 0;
+    // Last-layer support (general gates of the trailing run of disjoint gates,
+    // backward pass): lambda_l of column j starts as U|j>, which lives in j's
+    // particle-number sector, and only the later gates of the run have
+    // changed it, on their own qubits.  An item of gate l can be nonzero only
+    // if the bits outside those qubits and the gate's own (the stored bits in
+    // up_out / dn_out) can be completed to a state of j's sector: their up
+    // count c_u and down count c_d must satisfy c_u <= N_up(j) <= c_u + f_up
+    // and c_d <= N_dn(j) <= c_d + f_dn, where f_up / f_dn count the up / down
+    // qubits the run has touched.  N_up(j), N_dn(j) are the counts of j's
+    // bits in up_mask / dn_mask (a spinless chain: all qubits up).  tail = 0:
+    // every item.
+    int tail = 0;
+    int f_up = 0, f_dn = 0;
+    long long up_out = 0, dn_out = 0, up_mask = 0, dn_mask = 0;
 };
 
 // Arguments of one forward gate step over a tile.

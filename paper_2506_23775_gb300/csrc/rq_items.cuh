@@ -75,4 +75,19 @@ __device__ __forceinline__ bool item_offsets4(const GateGeom &geo, const int32_t
     return true;
 }
 
+// False for an item of a gate of the trailing run of disjoint gates whose
+// adjoint amplitudes are all zero in column b (see GateGeom::tail): x0 is the
+// item's amplitude index with the gate's bits clear.  Also false for a
+// padding column.  Only the backward kernels of general gates call this (the
+// marks are set for general gates only; a parity kernel leaves the check out
+// at compile time).
+__device__ __forceinline__ bool tail_live(const GateGeom &geo, const int32_t *cols, long long b, long long x0) {
+    if (!geo.tail || cols == nullptr) return true;
+    const long long j = cols[b];
+    if (j < 0) return false;
+    const int nu = __popcll(j & geo.up_mask), nd = __popcll(j & geo.dn_mask);
+    const int cu = __popcll(x0 & geo.up_out), cd = __popcll(x0 & geo.dn_out);
+    return cu <= nu && nu <= cu + geo.f_up && cd <= nd && nd <= cd + geo.f_dn;
+}
+
 }  // namespace rq

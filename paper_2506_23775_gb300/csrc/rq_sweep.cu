@@ -451,7 +451,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_base(const BwdArgs a) {
         pipelined_items(
             a.n_items,
             [&](long long it, long long (&off)[4]) {
-                return item_offsets4(a.geo, a.cols, it >> a.log2B, it & Bm, a.log2B, off);
+                return item_offsets4(a.geo, a.cols, it >> a.log2B, it & Bm, a.log2B, off) &&
+                       (MODE != kGeneral || tail_live(a.geo, a.cols, it & Bm, off[0] >> a.log2B));
             },
             [&](const long long (&off)[4], int st) {
 #pragma unroll
@@ -576,7 +577,8 @@ __global__ void __launch_bounds__(kThreads, MODE == kGeneral ? 1 : 2) k_bwd_dir(
         pipelined_items(
             a.n_items,
             [&](long long it, long long (&off)[4]) {
-                return item_offsets4(a.geo, a.cols, it >> a.log2B, it & Bm, a.log2B, off);
+                return item_offsets4(a.geo, a.cols, it >> a.log2B, it & Bm, a.log2B, off) &&
+                       (MODE != kGeneral || tail_live(a.geo, a.cols, it & Bm, off[0] >> a.log2B));
             },
             [&](const long long (&off)[4], int st) {
 #pragma unroll

@@ -659,7 +659,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_dir_df2(const BwdArgs a) {
     long long off[4], nxt[4];
     bool ok = false;
     if (it < a.n_items) {
-        ok = item_offsets4(a.geo, a.cols, it >> a.log2B, it & Bm, a.log2B, off);
+        ok = item_offsets4(a.geo, a.cols, it >> a.log2B, it & Bm, a.log2B, off) &&
+             (MODE != kGeneral || tail_live(a.geo, a.cols, it & Bm, off[0] >> a.log2B));
         if (ok) issue(off, 0);
     }
     cp_async_commit_df();
@@ -668,7 +669,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_dir_df2(const BwdArgs a) {
         __syncwarp(pair_mask);  // both lanes have read the stage about to be refilled
         bool ok_next = false;
         if (it + stride < a.n_items) {
-            ok_next = item_offsets4(a.geo, a.cols, (it + stride) >> a.log2B, (it + stride) & Bm, a.log2B, nxt);
+            ok_next = item_offsets4(a.geo, a.cols, (it + stride) >> a.log2B, (it + stride) & Bm, a.log2B, nxt) &&
+                      (MODE != kGeneral || tail_live(a.geo, a.cols, (it + stride) & Bm, nxt[0] >> a.log2B));
             if (ok_next) issue(nxt, st ^ 1);
         }
         cp_async_commit_df();
@@ -778,7 +780,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_base_df2(const BwdArgs a) {
     long long off[4], nxt[4];
     bool ok = false;
     if (it < a.n_items) {
-        ok = item_offsets4(a.geo, a.cols, it >> a.log2B, it & Bm, a.log2B, off);
+        ok = item_offsets4(a.geo, a.cols, it >> a.log2B, it & Bm, a.log2B, off) &&
+             (MODE != kGeneral || tail_live(a.geo, a.cols, it & Bm, off[0] >> a.log2B));
         if (ok) issue(off, 0);
     }
     cp_async_commit_df();
@@ -787,7 +790,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_base_df2(const BwdArgs a) {
         __syncwarp(pair_mask);  // both lanes have read the stage about to be refilled
         bool ok_next = false;
         if (it + stride < a.n_items) {
-            ok_next = item_offsets4(a.geo, a.cols, (it + stride) >> a.log2B, (it + stride) & Bm, a.log2B, nxt);
+            ok_next = item_offsets4(a.geo, a.cols, (it + stride) >> a.log2B, (it + stride) & Bm, a.log2B, nxt) &&
+                      (MODE != kGeneral || tail_live(a.geo, a.cols, (it + stride) & Bm, nxt[0] >> a.log2B));
             if (ok_next) issue(nxt, st ^ 1);
         }
         cp_async_commit_df();

@@ -26,7 +26,7 @@ EXPORTS = ("rq_create", "rq_destroy", "rq_setup_target", "rq_set_columns", "rq_s
            "rq_batch_add", "rq_batch_set_tile", "rq_batch_set_grid", "rq_batch_grid_info", "rq_batch_hvp", "rq_batch_info", "rq_batch_last_error",
            "rq_batch_set_fusion", "rq_batch_fusion_info",
            "rq_set_arithmetic", "rq_set_translation", "rq_hessian", "rq_set_checkpointing",
-           "rq_set_graphs", "rq_set_checks", "rq_set_first_layer", "rq_set_fusion", "rq_fusion_info",
+           "rq_set_graphs", "rq_set_checks", "rq_set_first_layer", "rq_set_last_layer", "rq_set_fusion", "rq_fusion_info",
            "rq_last_error")
 
 
@@ -106,6 +106,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "rq_set_graphs": ([vp, C.c_int], C.c_int),
         "rq_set_checks": ([vp, C.c_int], C.c_int),
         "rq_set_first_layer": ([vp, C.c_int], C.c_int),
+        "rq_set_last_layer": ([vp, C.c_int], C.c_int),
         "rq_set_fusion": ([vp, C.c_int], C.c_int),
         "rq_fusion_info": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
         "rq_batch_create": ([C.POINTER(vp), C.c_int], C.c_int),
@@ -231,6 +232,10 @@ class Context:
     def set_first_layer(self, enable: bool):
         """Sweep only the nonzero items of the first layer's gates (default on)."""
         self._check(self._lib.rq_set_first_layer(self._h, 1 if enable else 0))
+
+    def set_last_layer(self, enable: bool):
+        """Skip the zero-adjoint items of the last layer's gates in the backward sweep (default on)."""
+        self._check(self._lib.rq_set_last_layer(self._h, 1 if enable else 0))
 
     def set_fusion(self, max_window_qubits: int):
         self._check(self._lib.rq_set_fusion(self._h, int(max_window_qubits)))

@@ -1,7 +1,7 @@
 """Every switch of a context crossed with the others: arithmetic (FP64,
 double-float), forward-pass fusion (off, window of 5 qubits), sweep grid
 (fill the GPU, 8 items per thread), checkpointing (every state, every third),
-first-layer support (on, off) -- for general and parity gates with tiles and
+first-layer and last-layer support (on, off) -- for general and parity gates with tiles and
 direction chunks.  Each combination against the oracle at 1e-12 (f, the
 Riemannian gradient, two HVPs), and the FP64 combinations with each other at
 1e-13 (they differ only in rounding order)."""
@@ -15,7 +15,7 @@ from tests._helpers import assert_close, oracle_eval
 
 pytestmark = pytest.mark.gpu
 
-COMBOS = list(itertools.product((0, 1), (0, 5), (0, 8), (1, 3), (True, False)))
+COMBOS = list(itertools.product((0, 1), (0, 5), (0, 8), (1, 3), (True, False), (True, False)))
 
 
 @pytest.fixture(scope="module")
@@ -33,12 +33,14 @@ def test_all_switch_combinations(rq, structure):
     ref = None
     with rq.Context(0) as ctx:
         ctx.setup_problem(prob)
-        for arith, fusion, grid, ckpt, first in COMBOS:
-            what = f"structure {structure} arith {arith} fusion {fusion} grid {grid} ckpt {ckpt} first {first}"
+        for arith, fusion, grid, ckpt, first, last in COMBOS:
+            what = (f"structure {structure} arith {arith} fusion {fusion} grid {grid} ckpt {ckpt} first {first} "
+                    f"last {last}")
             ctx.set_arithmetic(arith)
             ctx.set_fusion(fusion)
             ctx.set_checkpointing(ckpt)
             ctx.set_first_layer(first)
+            ctx.set_last_layer(last)
             ctx.set_tile(64, 1)          # several tiles (and both parities), two direction chunks
             ctx.set_grid(grid)
             f, g, hv = ctx.hvp(prob.gates, X)
