@@ -37,17 +37,17 @@ FP64_PEAK_TFLOPS = 4 * 152 * 2.07e9 / 1e12
 FP32_PIPE_TOPS = 128 * 152 * 2.07e9 / 1e12   # FP32 pipe instructions per second (one FMA = one)
 HBM_FALLBACK_GBS = 6800.0
 
-# DRAM traffic of one full (not first-layer) FP64 bwd_gate_dir launch of this
-# workload (2^14 x 512 items: n = 16, general gates, 512-column tile):
-# dram__bytes_read.sum + dram__bytes_write.sum of the same kernel captured at
-# n = 14 (2^12 x 512 items: 536.98 + 111.07 MB) scaled by the items, 4x (the
-# DRAM-traffic ncu summary under profiles/).  Algorithmic bytes of that
-# launch: 2^14 * 512 * 5 * 4 * 16 = 2.684e9.  The figure holds only for the
-# kernel source it was taken on, so the sources are hashed and compared at
-# run time.
-TRAFFIC = {"kernel": "bwd_gate_dir", "bytes_per_launch": 2592171008,
+# DRAM traffic of one full FP64 bwd_gate_dir launch (neither first- nor
+# last-layer: every item swept) of this workload (2^14 x 512 items: n = 16,
+# general gates, 512-column tile): dram__bytes_read.sum +
+# dram__bytes_write.sum of the same kernel captured at n = 14 (2^12 x 512
+# items: 537.29 + 111.59 MB) scaled by the items, 4x (the DRAM-traffic ncu
+# summary under profiles/).  Algorithmic bytes of that launch:
+# 2^14 * 512 * 5 * 4 * 16 = 2.684e9.  The figure holds only for the kernel
+# source it was taken on, so the sources are hashed and compared at run time.
+TRAFFIC = {"kernel": "bwd_gate_dir", "bytes_per_launch": 2595516416,
            "algorithmic_bytes_per_launch": 2684354560,
-           "sha256": "9b3c9d6b7a9a9a3fe8ba5ba2ee50299b06310570bdb40d4f25df349a97be16a6",
+           "sha256": "cc5612f18b98fa48e1c109fa0d930f9e6a658ad12841b2a2ae37e21c552b1fdd",
            "sources": ("paper_2506_23775_gb300/csrc/rq_sweep.cu", "paper_2506_23775_gb300/csrc/rq_items.cuh",
                        "paper_2506_23775_gb300/csrc/rq_internal.h")}
 
@@ -747,7 +747,7 @@ def run_ours(args):
         if (headline and TRAFFIC["bytes_per_launch"] and dom == TRAFFIC["kernel"] and res["B"] == 512
                 and (args.sites, args.depth) == (8, 11) and _kernel_sources_sha256() == TRAFFIC["sha256"]):
             traffic = TRAFFIC["bytes_per_launch"]
-            traffic_note = ("DRAM bytes of one full (not first-layer) launch, scaled by items from an ncu capture "
+            traffic_note = ("DRAM bytes of one full (neither first- nor last-layer) launch, scaled by items from an ncu capture "
                             "at n = 14; that launch's algorithmic bytes: %d" % TRAFFIC["algorithmic_bytes_per_launch"])
         per_launch_ms = d["ms"] / d["launches"]
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
