@@ -311,8 +311,13 @@ rq_status eval_dev(rq_ctx *ctx, const double *gates, const double *dirs, int k, 
                     a.n_items = (long long)B << __builtin_popcountll(geo.free_bits);
                 }
                 // last-layer support: the kernels skip the items whose adjoint
-                // amplitudes are zero (they read the column table for j)
-                if (geo.tail) a.cols = cols;
+                // amplitudes are zero (they read the column table for j); a
+                // gate of both runs enumerates its restricted items only when
+                // first-layer support is on
+                if (geo.tail) {
+                    a.cols = cols;
+                    if (!first_layer) a.geo.restricted = 0;
+                }
                 // items with work, for the profile's algorithmic counts
                 const double live = ctx->prof_on && geo.tail && !(geo.restricted && first_layer)
                                         ? tail_items(ctx, geo, ti) : (double)a.n_items;

@@ -109,3 +109,25 @@ def test_skipped_items_match_bruteforce(rq):
     # per general-gate item: direction step 64 complex multiply-adds, base step 32 (8 flops each)
     assert flops[False][0] - flops[True][0] == pytest.approx(zeros * 512.0, rel=1e-12)
     assert flops[False][1] - flops[True][1] == pytest.approx(zeros * 256.0, rel=1e-12)
+
+
+@pytest.mark.parametrize("structure", [0, 1])
+def test_gates_in_both_runs(rq, structure):
+    """A one-layer circuit: every gate is in the leading and in the trailing
+    run of disjoint gates.  Every combination of first- and last-layer
+    support gives the same results, and the oracle's."""
+    prob = w.make_problem(4, 1, 0.6, seed=921, structure=structure)
+    X = w.random_directions(prob.n_params, 2, 922)
+    f0, g0, h0, _ = oracle_eval(prob, range(1 << prob.n), X, chunk=64)
+    with rq.Context(0) as ctx:
+        ctx.setup_problem(prob)
+        ctx.set_tile(64, 2)
+        for first in (True, False):
+            for last in (True, False):
+                what = f"structure {structure} first {first} last {last}"
+                ctx.set_first_layer(first)
+                ctx.set_last_layer(last)
+                f, g, hv = ctx.hvp(prob.gates, X)
+                assert abs(f - f0) <= 1e-12 * max(abs(f0), 1e-6 * 2 ** prob.n), what
+                assert_close(g, g0, prob.n, what=what + " grad")
+                assert_close(hv, h0, prob.n, what=what + " hvp")
