@@ -219,9 +219,9 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)   # before the process group: NCCL binds this rank to its own GPU
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
-    torch.cuda.set_device(local)
 
     from paper_2506_23775_gb300 import _build
     if rank == 0 or local == 0:
